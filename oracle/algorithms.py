@@ -1,0 +1,387 @@
+"""Plain CPU restatement of alternating cross interpolation (ACI), Appendix B.
+
+TEST INFRASTRUCTURE ONLY (see the package header): imported by tests/,
+__graft_entry__.smoke() and bench.py's CPU-baseline leg, never by the library.
+
+Everything is FP64 / complex128 numpy, written in the order and notation of the
+paper's Algorithms 1-5, with 0-based sites s = 0..L-1 (the paper's site l = s + 1).
+Index sets are kept as lists of multi-index tuples, exactly as defined in Sec. 2.5:
+I_s holds tuples (sigma_0..sigma_s) and J_s holds tuples (sigma_s..sigma_{L-1}).
+Frames are rebuilt from the index sets with Algorithm 5 at every step (no caching).
+
+Readings of places where the paper is silent or garbled (each is listed in the design doc):
+  R1  tol is relative by default: tau = tol * S, S the running max |Pi| over all Pi
+      blocks formed so far in the call; tol_kind="abs" gives Alg. 1's absolute tau.
+      The initial-guess CI uses tau = tol * max|M| of its own matrix (or tol for "abs").
+  R2  Alg. 2 stops *before* accepting a pivot with |pivot| <= tau, or once chi_hat pivots
+      are taken; epsilon is the magnitude of the first rejected pivot (the largest
+      remaining Schur entry), 0 when the Schur block is empty.
+  R3  Alg. 2's second swap exchanges J_j (not J_i) with J_chi; Alg. 3's L_{I,1:n} and
+      U_{1:m,J} are the k x k blocks L_{I,1:k}, U_{1:k,J}.  L and U are unit triangular:
+      L_{rp} = S_{rp}/S_{pp}, U_{pc} = S_{pc}/S_{pp} from the in-place elimination.
+  R4  At least one pivot is always taken. Pivot search maximises |v| (real) or
+      re^2 + im^2 (complex, each product and the sum rounded separately); exact ties
+      go to the lowest original linear index row * n + col. A zero pivot (all-zero
+      block) gives unit L/U columns, D = 0, and D^-1 is read as 0.
+  R5  Alg. 1 writes I_l and J_{l+1} at bond l (Sec. 2.6 prose says I_{l+1}, J_l).
+  R6  The output is y = T_0 P_0^-1 T_1 P_1^-1 ... T_{L-1} from the last right-to-left
+      sweep: Y_0 = A_0 = L L_I^-1 of bond 0, Y_s = B_{s-1} P_s^-1 with
+      B_{s-1} = L_I D U of bond s-1 and P_s = L_I D U_J of bond s, Y_{L-1} = B_{L-2}.
+  R7  The CI-canonicalisation of Y^init uses CI "right", keeps J_l, and multiplies
+      A = L D U_J into Y_{l-1}.
+  R8  maxiter defaults to 20; epsilon of an iteration is the max over both half-sweeps;
+      ranks are compared with those at the end of the previous iteration (after the
+      initial CI for the first). A second stop: an iteration that reproduces every J
+      set of the previous one is a fixed point (the next sweep would repeat it exactly).
+  R9  Y^init is the counter-based SplitMix64 TT of oracle.rng with ranks
+      min(chi_hat, min_n r^n_s), unless the caller passes one.
+
+Parity pins (tests/test_oracle_*.py): LDU against an independent complete-pivoting LU
+and brute-force residual identities; CI factors against exact interpolation on the
+pivot cross; ACI against dense brute force on small grids, closed-form Fourier and
+Gaussian products (Eqs. (gaussians), (fouriermultiplication)), exact low-rank products,
+commutativity and the interpolation property of the CI-canonical form.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+from scipy.linalg import solve_triangular
+
+from .rng import random_tt_counter
+
+# ---------------------------------------------------------------- elementwise f (Sec. 2.1)
+
+OPS = ("mul", "mul_conj", "abs2_mul", "affine")
+
+
+def apply_op(op: str, xs, coef=None):
+    """f(x^1, ..., x^N) entrywise: a*b, a*conj(b), |a|^2 a, or c0 + c1 a + c2 b + c3 a b."""
+    a = xs[0]
+    b = xs[1] if len(xs) > 1 else None
+    if op == "mul":
+        return a * b
+    if op == "mul_conj":
+        return a * np.conj(b)
+    if op == "abs2_mul":
+        if np.iscomplexobj(a):
+            return (a.real * a.real + a.imag * a.imag) * a
+        return (a * a) * a
+    if op == "affine":
+        c0, c1, c2, c3 = coef
+        return c0 + c1 * a + c2 * b + c3 * (a * b)
+    raise ValueError(op)
+
+
+def magnitude(v):
+    """|v|: fabs for real, sqrt(re*re + im*im) for complex (no fused operations)."""
+    v = np.asarray(v)
+    if np.iscomplexobj(v):
+        return np.sqrt(v.real * v.real + v.imag * v.imag)
+    return np.abs(v)
+
+
+def pivot_key(v):
+    """Quantity maximised by the pivot search (R4)."""
+    v = np.asarray(v)
+    if np.iscomplexobj(v):
+        return v.real * v.real + v.imag * v.imag
+    return np.abs(v)
+
+
+# ---------------------------------------------------------------- Algorithm 2: LDU (prrLU)
+
+def ldu(M, tau: float, chimax: int):
+    """Algorithm 2: in-place LDU with full-search pivoting (readings R2-R4).
+
+    Returns a dict with
+      L  (m x k) unit lower triangular in pivot order, rows in M's original row order,
+      D  (k,)   pivots,
+      U  (k x n) unit upper triangular in pivot order, columns in M's original order,
+      I, J      pivot row / column positions of M in pivot order,
+      eps       error estimate, k the rank,
+      best, second  per accepted pivot: its magnitude and the next-largest candidate's.
+    """
+    S = np.array(M, copy=True)
+    m, n = S.shape
+    I = np.arange(m)  # I[pos] = original row now at position pos
+    J = np.arange(n)
+    chi = 0
+    eps = 0.0
+    best_list, second_list = [], []
+    while True:
+        if chi == min(m, n):
+            eps = 0.0
+            break
+        sub = S[chi:, chi:]
+        key = pivot_key(sub)
+        kbest = key.max()
+        where = np.argwhere(key == kbest)
+        lin = I[chi + where[:, 0]] * n + J[chi + where[:, 1]]
+        i, j = where[int(np.argmin(lin))] + chi
+        piv = S[i, j]
+        mag = float(magnitude(piv))
+        if chi == chimax or (chi >= 1 and mag <= tau):
+            eps = mag
+            break
+        flat = key.reshape(-1).copy()
+        flat[(i - chi) * (n - chi) + (j - chi)] = -np.inf
+        sec = float(flat.max()) if flat.size > 1 else -np.inf
+        if np.iscomplexobj(S) and sec > -np.inf:
+            sec = float(np.sqrt(sec))
+        best_list.append(mag)
+        second_list.append(sec)
+        # swap the pivot to position (chi, chi) in M, and in I and J (R3: J_j, not J_i)
+        S[[i, chi], :] = S[[chi, i], :]
+        S[:, [j, chi]] = S[:, [chi, j]]
+        I[[i, chi]] = I[[chi, i]]
+        J[[j, chi]] = J[[chi, j]]
+        # Schur complement (Gaussian elimination step)
+        if piv != 0:
+            l = S[chi + 1:, chi] / S[chi, chi]
+            S[chi + 1:, chi + 1:] -= np.outer(l, S[chi, chi + 1:])
+        chi += 1
+    k = chi
+    D = np.array([S[p, p] for p in range(k)], dtype=S.dtype)
+    Lp = np.zeros((m, k), dtype=S.dtype)
+    Up = np.zeros((k, n), dtype=S.dtype)
+    for p in range(k):
+        if D[p] != 0:
+            Lp[p + 1:, p] = S[p + 1:, p] / D[p]
+            Up[p, p + 1:] = S[p, p + 1:] / D[p]
+        Lp[p, p] = 1
+        Up[p, p] = 1
+    L = np.zeros_like(Lp)
+    U = np.zeros_like(Up)
+    L[I, :] = Lp  # undo the row permutation: L[I[pos]] = Lp[pos]
+    U[:, J] = Up
+    return dict(L=L, D=D, U=U, I=I[:k].copy(), J=J[:k].copy(), eps=eps, k=k,
+                best=np.array(best_list), second=np.array(second_list))
+
+
+# ---------------------------------------------------------------- Algorithm 3: CI
+
+def _inv_diag(D):
+    out = np.zeros_like(D)
+    nz = D != 0
+    out[nz] = 1.0 / D[nz]
+    return out
+
+
+def crossinterpolate(M, tau: float, chimax: int, leftorright: str = "right"):
+    """Algorithm 3: A, B with A @ B = L D U ~ M; "left" puts P^-1 into A, "right" into B."""
+    f = ldu(M, tau, chimax)
+    L, D, U, I, J = f["L"], f["D"], f["U"], f["I"], f["J"]
+    if leftorright == "left":
+        LI = L[I, :]  # k x k unit lower
+        # A = L LI^-1  <=>  LI^T A^T = L^T
+        A = solve_triangular(LI.T, L.T, lower=False, unit_diagonal=True).T
+        B = LI @ (D[:, None] * U)
+    else:
+        UJ = U[:, J]  # k x k unit upper
+        A = L @ (D[:, None] * UJ)
+        B = solve_triangular(UJ, U, lower=False, unit_diagonal=True)
+    f.update(A=A, B=B)
+    return f
+
+
+# ---------------------------------------------------------------- Algorithm 4: local update
+
+def localupdate(Pi, tau: float, chimax: int, leftorright: str):
+    """Algorithm 4: reshape Pi[alpha, s, s', beta] to M[(alpha, s), (s', beta)] and factorise."""
+    a, d1, d2, b = Pi.shape
+    M = Pi.reshape(a * d1, d2 * b)
+    f = crossinterpolate(M, tau, chimax, leftorright)
+    k = f["k"]
+    f["Y"] = f["A"].reshape(a, d1, k)
+    f["Y2"] = f["B"].reshape(k, d2, b)
+    return f
+
+
+# ---------------------------------------------------------------- Algorithm 5: frames
+
+def leftframe(X, Lf, Iprev, Inew):
+    """Algorithm 5 (left): L'_{(i,s),beta} = L_{i,gamma} X^s_{gamma,beta}, then keep rows Inew."""
+    d = X.shape[1]
+    Lp = np.einsum("ig,gsb->isb", Lf, X).reshape(-1, X.shape[2])
+    pos = {t: q for q, t in enumerate(Iprev)}
+    rows = [pos[t[:-1]] * d + t[-1] for t in Inew]  # KeyError if nesting is violated
+    return Lp[rows, :]
+
+
+def rightframe(X, Rf, Jnext, Jnew):
+    """Algorithm 5 (right): R'_{alpha,(s,j)} = X^s_{alpha,gamma} R_{gamma,j}, then keep columns Jnew."""
+    Rp = np.einsum("asg,gj->asj", X, Rf).reshape(X.shape[0], -1)
+    pos = {t: q for q, t in enumerate(Jnext)}
+    cols = [t[0] * len(Jnext) + pos[t[1:]] for t in Jnew]
+    return Rp[:, cols]
+
+
+def pi_tensor(Lf, X1, X2, Rf):
+    """Eq. (pifromframes): Pi[alpha, s, s', beta] = L X_l X_{l+1} R, as (L X_l)(X_{l+1} R)."""
+    r1 = X1.shape[2]
+    LX = (Lf @ X1.reshape(X1.shape[0], -1)).reshape(-1, r1)
+    XR = X2.reshape(-1, X2.shape[2]) @ Rf
+    XR = XR.reshape(r1, -1)
+    return (LX @ XR).reshape(Lf.shape[0], X1.shape[1], X2.shape[1], Rf.shape[1])
+
+
+# ---------------------------------------------------------------- Algorithm 1: ACI
+
+def init_guess(inputs, chimax: int, seed: int, complex_values: bool):
+    """R9: counter-based random TT with bonds min(chi_hat, min_n r^n_s)."""
+    L = len(inputs[0])
+    dims = [c.shape[1] for c in inputs[0]]
+    ranks = [1]
+    for s in range(1, L):
+        ranks.append(min([chimax] + [int(x[s].shape[0]) for x in inputs]))
+    ranks.append(1)
+    return random_tt_counter(seed, ranks, dims, complex_values)
+
+
+def _maxabs(a) -> float:
+    return float(magnitude(a).max()) if a.size else 0.0
+
+
+def assemble_output(factors, L: int):
+    """R6: Y_0 = A_0, Y_s = B_{s-1} P_s^-1 (1 <= s <= L-2), Y_{L-1} = B_{L-2}."""
+    Y = [None] * L
+    if L == 1:
+        return [factors["single"]]
+    f0 = factors[0]
+    Y[0] = f0["A"].reshape(1, -1, f0["k"])
+    for s in range(1, L):
+        B = factors[s - 1]["B"]  # k_{s-1} x (d_s * k_s)
+        kprev = B.shape[0]
+        if s == L - 1:
+            Y[s] = B.reshape(kprev, -1, 1)
+            continue
+        fs = factors[s]
+        k = fs["k"]
+        X = B.reshape(-1, k)  # rows (alpha, sigma_s), columns J_{s+1}
+        LI = fs["L"][fs["I"], :]
+        UJ = fs["U"][:, fs["J"]]
+        # X P^-1 with P = LI D UJ:  W UJ = X,  Z LI = W D^-1
+        W = solve_triangular(UJ.T, X.T, lower=True, unit_diagonal=True).T
+        W = W * _inv_diag(fs["D"])[None, :]
+        Z = solve_triangular(LI.T, W.T, lower=False, unit_diagonal=True).T
+        Y[s] = Z.reshape(kprev, -1, k)
+    return Y
+
+
+def aci(inputs, op: str = "mul", tol: float = 1e-10, max_rank: int = 64, *,
+        tol_kind: str = "rel", maxiter: int = 20, coef=None, init=None, seed: int = 0,
+        record: bool = False):
+    """Algorithm 1: alternating cross interpolation of f(X^1, ..., X^N).
+
+    ``inputs`` is a list of N TTs (lists of cores (r, d, r')). Returns a dict with the
+    output cores ``Y``, the ranks, the final pivot positions per bond (``I_pos``,
+    ``J_pos``: row / column positions in that bond's Pi matrix, from the last sweep),
+    ``eps`` per bond (last iteration, both half-sweeps), ``iterations``, ``S`` and, if
+    ``record``, the per-pivot magnitudes needed to detect near-ties.
+    """
+    N = len(inputs)
+    L = len(inputs[0])
+    dims = [c.shape[1] for c in inputs[0]]
+    for x in inputs:
+        assert len(x) == L and [c.shape[1] for c in x] == dims
+    cplx = any(np.iscomplexobj(c) for x in inputs for c in x)
+    if coef is not None and np.iscomplexobj(np.asarray(coef)):
+        cplx = True
+    dt = np.complex128 if cplx else np.float64
+    X = [[np.asarray(c, dtype=dt) for c in x] for x in inputs]
+    chimax = int(max_rank)
+    rel = tol_kind == "rel"
+
+    def fvals(blocks):
+        return apply_op(op, blocks, coef)
+
+    if L == 1:
+        y = fvals([x[0] for x in X]).astype(dt)
+        return dict(Y=[y], ranks=[1, 1], iterations=0, eps=[], I_pos=[], J_pos=[], S=_maxabs(y))
+
+    Yinit = init if init is not None else init_guess(X, chimax, seed, cplx)
+    Y = [np.asarray(c, dtype=dt).copy() for c in Yinit]
+
+    # index sets: I[s] over sites 0..s, J[s] over sites s..L-1; I[-1] = J[L] = [()]
+    I = {-1: [()]}
+    J = {L: [()]}
+    Lf = [{-1: np.ones((1, 1), dtype=dt)} for _ in range(N)]
+    Rf = [{L: np.ones((1, 1), dtype=dt)} for _ in range(N)]
+
+    # ---- CI-canonicalisation of the initial guess, right to left (R7)
+    for s in range(L - 1, 0, -1):
+        r = Y[s].shape[0]
+        M = Y[s].reshape(r, -1)
+        tau0 = tol * _maxabs(M) if rel else tol
+        f = crossinterpolate(M, tau0, chimax, "right")
+        nj = len(J[s + 1])
+        J[s] = [(int(q) // nj,) + J[s + 1][int(q) % nj] for q in f["J"]]
+        Y[s] = f["B"].reshape(f["k"], dims[s], nj)
+        Y[s - 1] = np.tensordot(Y[s - 1], f["A"], axes=(2, 0))
+        for n in range(N):
+            Rf[n][s] = rightframe(X[n][s], Rf[n][s + 1], J[s + 1], J[s])
+
+    S = 0.0
+    ranks_prev = [len(J[s]) for s in range(1, L)]
+    J_prev = {s: list(J[s]) for s in range(1, L)}
+    iterations = 0
+    eps_lr = [0.0] * (L - 1)
+    eps_rl = [0.0] * (L - 1)
+    factors = {}
+    I_pos = [None] * (L - 1)
+    J_pos = [None] * (L - 1)
+    log = []
+
+    def bond(b, direction):
+        nonlocal S
+        blocks = [pi_tensor(Lf[n][b - 1], X[n][b], X[n][b + 1], Rf[n][b + 2]) for n in range(N)]
+        Pi = fvals(blocks).astype(dt)
+        S = max(S, _maxabs(Pi))
+        tau = tol * S if rel else tol
+        f = localupdate(Pi, tau, chimax, direction)
+        ni = len(I[b - 1])
+        nj = len(J[b + 2])
+        I[b] = [I[b - 1][int(q) // dims[b]] + (int(q) % dims[b],) for q in f["I"]]
+        J[b + 1] = [(int(q) // nj,) + J[b + 2][int(q) % nj] for q in f["J"]]
+        Y[b] = f["Y"]
+        Y[b + 1] = f["Y2"]
+        if record:
+            log.append(dict(bond=b, direction=direction, S=S, tau=tau, k=f["k"], eps=f["eps"],
+                            best=f["best"], second=f["second"], I=f["I"].copy(), J=f["J"].copy()))
+        return f
+
+    for it in range(1, maxiter + 1):
+        iterations = it
+        for b in range(0, L - 1):  # left-to-right sweep
+            f = bond(b, "right")
+            eps_lr[b] = f["eps"]
+            for n in range(N):
+                Lf[n][b] = leftframe(X[n][b], Lf[n][b - 1], I[b - 1], I[b])
+        for b in range(L - 2, -1, -1):  # right-to-left sweep
+            f = bond(b, "left")
+            eps_rl[b] = f["eps"]
+            factors[b] = f
+            I_pos[b] = f["I"].copy()
+            J_pos[b] = f["J"].copy()
+            for n in range(N):
+                Rf[n][b + 1] = rightframe(X[n][b + 1], Rf[n][b + 2], J[b + 2], J[b + 1])
+        ranks = [len(J[s]) for s in range(1, L)]
+        tau = tol * S if rel else tol
+        emax = max(max(eps_lr), max(eps_rl))
+        grew = any(r > q for r, q in zip(ranks, ranks_prev))
+        fixed = all(J[s] == J_prev[s] for s in range(1, L))
+        if (not grew and emax <= tau) or fixed:
+            break
+        ranks_prev = ranks
+        J_prev = {s: list(J[s]) for s in range(1, L)}
+
+    Yout = assemble_output(factors, L)
+    out = dict(Y=Yout, ranks=[1] + [len(J[s]) for s in range(1, L)] + [1], iterations=iterations,
+               eps=[max(a, b) for a, b in zip(eps_lr, eps_rl)], eps_lr=list(eps_lr),
+               eps_rl=list(eps_rl), I_pos=I_pos, J_pos=J_pos, S=S,
+               I_sets={s: list(I[s]) for s in range(0, L - 1)},
+               J_sets={s: list(J[s]) for s in range(1, L)})
+    if record:
+        out["log"] = log
+    return out
