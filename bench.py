@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Benchmark of one ACI product f(A, B) = A * B on GB300 (replicas across GPUs).
+
+Workload (default): 2D interleaved quantics TTs, L = 40 sites (2 x 20 bits), d = 2, FP64 real,
+seeded 200-mode Fourier fields (|k| <= 32, amplitudes N(0,1) exp(-|k|^2/100)) as exact block
+sums, TT-SVD to rank chi = 128; op a*b, tol 1e-10 relative, max_rank 2 chi = 256, at most 20
+sweeps. One step = one whole ACI call (initial guess, sweeps, stop tests, output assembly)
+through the C ABI on device-resident inputs.
+
+Prints one JSON line (rank 0). `value` = products per second over all ranks. The L2 cache is
+flushed (a 256 MB write, outside the timed events) before every timed step. The `roofline`
+object is for the kernel class with the largest share of device time, from CUDA events recorded
+by the library on its stream around every launch during the timed steps. `cpu_baseline` times
+the CPU oracle on a bounded sample of the same workload on this host.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ACI f(A,B) time vs χ at rel err ≤1e-8 (FP64 vs mixed/learned); % tensor peak"
+UNIT = "products/s"
+# FP64 vector peak of a GB300 (nominal 1.25 TFLOP/s: 152 SMs x ~2 DFMA/clk/SM at ~2.06 GHz);
+# a probe on this pool measured 1.197 TFLOP/s of DFMA throughput.
+FP64_PEAK_TFLOPS = 1.25
+SAMPLE_ITERS = 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--chi", type=int, default=128)
+    ap.add_argument("--max-sweeps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(chi):
+    from synthetic import config_inputs
+    p = config_inputs(2, chi)
+    return p
+
+
+def config_dict(args, p):
+    return {"workload": f"2D interleaved quantics FP64 Fourier fields, L=40 d=2, chi={args.chi}, "
+                        f"a*b, tol {p['tol']:g} rel, max_rank {p['max_rank']}, <= {args.max_sweeps} sweeps",
+            "L": 40, "d": 2, "chi": args.chi, "max_rank": p["max_rank"], "tol": p["tol"],
+            "op": "a*b", "max_sweeps": args.max_sweeps,
+            "l2": "flushed before every timed step (256 MB write, untimed)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(p, max_sweeps):
+    """Time the oracle on the first SAMPLE_ITERS sweeps of the product; extrapolate to a product.
+
+    Returns (estimated seconds per product, sample seconds, threads)."""
+    import oracle
+    a, b = p["inputs"]
+    t0 = time.perf_counter()
+    oracle.aci([a, b], "mul", p["tol"], p["max_rank"], maxiter=SAMPLE_ITERS)
+    t = time.perf_counter() - t0
+    per_product = t * max_sweeps / SAMPLE_ITERS
+    return per_product, t
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info()]
+        return max(n) if n else 1
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = workload(args.chi)
+    for _ in range(args.warmup):
+        oracle_sample(p, args.max_sweeps)
+    est = []
+    for _ in range(args.steps):
+        per, t = oracle_sample(p, args.max_sweeps)
+        est.append(per)
+    value = len(est) / sum(est)
+    cores = blas_threads()
+    sample = (f"each step: the CPU oracle's initial CI and first {SAMPLE_ITERS} of {args.max_sweeps} sweeps of "
+              f"the same product; per-product time = sample time x {args.max_sweeps}/{SAMPLE_ITERS}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, p),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ our arm
+
+def source_hash(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel_class):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source still matches."""
+    f = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = {"pivot": "aci_prrlu.cu", "pi": "aci_gemm.cu", "frame": "aci_gemm.cu"}.get(kernel_class)
+    if not src or not os.path.exists(f):
+        return None
+    h = source_hash(os.path.join(ROOT, "paper_2604_00037_gb300", "csrc", src))
+    for line in open(f):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel_class and parts[1] == h:
+            return float(parts[2])
+    return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2604_00037_gb300.binding import Context
+
+    p = workload(args.chi)
+    a, b = p["inputs"]
+    A = [torch.from_numpy(c).cuda() for c in a]
+    B = [torch.from_numpy(c).cuda() for c in b]
+    ctx = Context(local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(profile):
+        return ctx.elementwise(A, B, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps, profile=profile)
+
+    for w in range(args.warmup):
+        flush.fill_(w & 0xFF)
+        step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, infos = [], []
+    for k in range(args.steps):
+        flush.fill_((k + 7) & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        y, info = step(True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        infos.append(info)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # per-kernel-class roofline from the library's CUDA events of the timed steps
+    classes = ("frame", "pi", "pivot", "other")
+    kms = {c: sum(i["kernels"][c]["ms"] for i in infos) for c in classes}
+    kcnt = {c: sum(i["kernels"][c]["count"] for i in infos) for c in classes}
+    kfl = {c: sum(i["kernels"][c]["flops"] for i in infos) for c in classes}
+    dom = max(("frame", "pi", "pivot"), key=lambda c: kms[c])
+    achieved = kfl[dom] / (kms[dom] / 1e3) / 1e12
+    traffic = recorded_traffic(dom)
+    roofline = {"bound": "alu", "kernel": {"frame": "gemm_kernel (frame half-products)",
+                                           "pi": "gemm_kernel (Pi block + f)",
+                                           "pivot": "prrlu_kernel"}[dom],
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": traffic * kcnt[dom] / max(kcnt[dom], 1) if traffic is not None else None,
+                "peak_source": "FP64 vector peak, nominal 1.25 TFLOP/s (no FP64 tensor path on GB300)",
+                "share": kms[dom] / total_ms * (world if world > 1 else 1),
+                "classes_ms_per_step": {c: kms[c] / args.steps for c in classes},
+                "classes_flops_per_step": {c: kfl[c] / args.steps for c in classes},
+                "classes_launches_per_step": {c: kcnt[c] / args.steps for c in classes}}
+
+    # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
+    ah = [torch.from_numpy(c).pin_memory().numpy() for c in a]
+    bh = [torch.from_numpy(c).pin_memory().numpy() for c in b]
+    h2d = sum(c.nbytes for c in ah) + sum(c.nbytes for c in bh)
+    ctx.elementwise(ah, bh, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps, out_memory="host")
+    e2e_t, d2h = [], 0
+    for k in range(max(1, min(args.steps, 3))):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        yh, _ = ctx.elementwise(ah, bh, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps,
+                                out_memory="host")
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+        d2h = sum(c.nbytes for c in yh)
+    e2e_value = len(e2e_t) / sum(e2e_t)
+    if world > 1:
+        t = torch.tensor([sum(e2e_t)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_value = world * len(e2e_t) / float(t.item())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per, t = oracle_sample(p, args.max_sweeps)
+        cpu = {"value": 1.0 / per, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": f"the CPU oracle's initial CI and first {SAMPLE_ITERS} of {args.max_sweeps} sweeps of one "
+                         f"product ({t:.1f} s); per-product time = sample x {args.max_sweeps}/{SAMPLE_ITERS}"}
+
+    last = infos[-1]
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_dict(args, p),
+                "result": {"iterations": last["iterations"], "converged": last["converged"],
+                           "max_rank": max(last["ranks"]), "max_eps_rel": last["max_eps"] / last["scale"]},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * aci.h - C ABI of the GB300 library for alternating cross interpolation (ACI).
+ *
+ * ACI (arXiv:2604.00037, Sec. 2 and Algorithm 1) computes a tensor train (TT) y with
+ * y[sigma] ~ f(x^1[sigma], ..., x^N[sigma]) for an elementwise function f of N <= 2 input
+ * TTs, in O(chi^3) per bond instead of the O(chi^4) of a Kronecker-delta contraction.
+ * Every step of the sweep runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point
+ *  - A TT has L sites; core s has shape rank[s] x d[s] x rank[s+1], stored row-major and
+ *    contiguous ([alpha][sigma][beta], sigma in the middle), rank[0] = rank[L] = 1 (Sec. 2.1).
+ *    Site 0 is the most significant quantics bit (Eq. (quanticsrep)).
+ *  - All calls are ordered on the context's CUDA stream. Input pointers are borrowed and
+ *    only read. Device pointers must belong to the context's device.
+ *  - No C++ exception crosses this interface. A negative status leaves outputs untouched
+ *    and sets a message readable with aci_last_error().
+ *  - Not thread-safe per context: one call at a time on a given aci_ctx.
+ */
+#ifndef ACI_H
+#define ACI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aci_ctx aci_ctx;
+
+/* Status codes. > 0: warning, the output is valid. < 0: error, the output is untouched. */
+typedef enum {
+    ACI_OK = 0,
+    ACI_W_NOT_CONVERGED = 1, /* max_sweeps reached before the stop test of Algorithm 1 held */
+    ACI_E_ARG = -1,          /* null pointer, bad enum, tol < 0, max_rank < 1, ...          */
+    ACI_E_SHAPE = -2,        /* inputs differ in L or d, rank[0] or rank[L] != 1, d < 1     */
+    ACI_E_DTYPE = -3,        /* unsupported dtype, mixed dtypes, complex coefficients on reals */
+    ACI_E_ALLOC = -4,        /* the allocator returned NULL                                 */
+    ACI_E_CUDA = -5,         /* a CUDA runtime call failed (message has the CUDA error)      */
+    ACI_E_TIMEOUT = -6,      /* a device-side wait exceeded its iteration limit             */
+    ACI_E_NUMERIC = -7       /* a non-finite value reached a pivot                         */
+} aci_status;
+
+typedef enum { ACI_R64 = 0, ACI_C128 = 1 } aci_dtype;           /* FP64 real, complex128 */
+typedef enum { ACI_MEM_DEVICE = 0, ACI_MEM_HOST = 1 } aci_memory;
+
+/* Elementwise functions f (Sec. 2.1). N = 2 except ABS2_MUL (N = 1, b ignored).
+ * AFFINE: f = c0 + c1 a + c2 b + c3 a b, complex coefficients c[i] = {re, im};
+ * for real dtypes every imaginary part must be 0. For real dtypes MUL_CONJ equals MUL. */
+typedef enum { ACI_OP_MUL = 0, ACI_OP_MUL_CONJ = 1, ACI_OP_ABS2_MUL = 2, ACI_OP_AFFINE = 3 } aci_op_kind;
+typedef struct {
+    int32_t kind;     /* aci_op_kind */
+    int32_t _pad;
+    double c[4][2];   /* AFFINE coefficients, ignored otherwise */
+} aci_op;
+
+typedef enum { ACI_TOL_REL = 0, ACI_TOL_ABS = 1 } aci_tol_kind;
+typedef enum { ACI_PIVOT_FULL = 0 } aci_pivot_mode;   /* full search of Algorithm 2 */
+typedef enum { ACI_PREC_FP64 = 0 } aci_precision;     /* every step in FP64 / complex128 */
+
+/* A tensor train. For inputs every field is set by the caller. For outputs the library
+ * fills it: d, rank and core are library-owned until aci_tt_release(). */
+typedef struct {
+    int32_t L;             /* number of sites, >= 1                                       */
+    int32_t dtype;         /* aci_dtype                                                    */
+    int32_t memory;        /* aci_memory: where core[s] points                             */
+    int32_t _pad;
+    const int32_t *d;      /* host array [L], local dimensions d[s] >= 1                    */
+    const int64_t *rank;   /* host array [L+1], rank[0] = rank[L] = 1                       */
+    void *const *core;     /* host array [L] of pointers to cores rank[s] x d[s] x rank[s+1] */
+} aci_tt;
+
+/* Optional controls of aci_elementwise_ex (aci_opts_default() fills the defaults). */
+typedef struct {
+    int32_t tol_kind;      /* ACI_TOL_REL (default): tau = tol * max|Pi| seen so far in the call;
+                              ACI_TOL_ABS: tau = tol, the absolute tolerance of Algorithm 1     */
+    int32_t max_sweeps;    /* maxiter of Algorithm 1 (default 20)                          */
+    int32_t pivot_mode;    /* aci_pivot_mode                                               */
+    int32_t precision;     /* aci_precision                                                */
+    uint64_t seed;         /* seed of the counter-based SplitMix64 initial guess            */
+    const aci_tt *init;    /* optional initial guess Y^init (warm start); NULL = random      */
+    int32_t out_memory;    /* aci_memory of the output cores (default device)              */
+    int32_t profile;       /* 1: time every kernel with CUDA events on the context stream and
+                              count its algorithmic flops (aci_stats.kernel_*); 0: off        */
+} aci_opts;
+
+/* Kernel classes of aci_stats.kernel_* (profile = 1). Flops are real-equivalent (a complex
+ * multiply-add counts 8) and algorithmic: what the step needs, not what the kernel issues. */
+typedef enum {
+    ACI_KCLASS_FRAME = 0,  /* frame half-products L X and X R (Algorithm 5, Eq. (framesrecursive)) */
+    ACI_KCLASS_PI = 1,     /* Pi block with f (Eq. (pifromframes), Eq. (localupdate))              */
+    ACI_KCLASS_PIVOT = 2,  /* rank-revealing LU (Algorithm 2); flops = Schur-update multiply-adds  */
+    ACI_KCLASS_OTHER = 3,  /* initial guess, stop test, output assembly                            */
+    ACI_KCLASS_N = 4
+} aci_kernel_class;
+
+/* Optional diagnostics. Host arrays may be NULL; when given they must hold the sizes noted. */
+typedef struct {
+    int32_t iterations;    /* sweeps (left-to-right + right-to-left) performed              */
+    int32_t converged;     /* 1 if the stop test of Algorithm 1 held                       */
+    int32_t fixed_point;   /* 1 if an iteration reproduced every J set of the previous one  */
+    int32_t L;
+    double max_eps;        /* max over bonds of the last iteration's error estimates        */
+    double scale;          /* S = max |Pi| over the call                                    */
+    double tau;            /* final absolute tolerance                                      */
+    double device_ms;      /* device time of the call (CUDA events), 0 if not measured       */
+    int64_t kernel_launches; /* kernels the call launched                                     */
+    int64_t *ranks;        /* [L+1] output ranks                                            */
+    double *eps;           /* [L-1] per-bond error estimate of the last iteration (max of the two half-sweeps) */
+    int32_t *pivot_rows;   /* [(L-1) * max_rank]: bond b's final pivot rows (positions in its Pi matrix) */
+    int32_t *pivot_cols;   /* [(L-1) * max_rank]: bond b's final pivot columns                            */
+    double kernel_ms[4];   /* profile = 1: summed device time per aci_kernel_class              */
+    int64_t kernel_count[4];   /* launches per class (always filled)                           */
+    double kernel_flops[4];    /* profile = 1: algorithmic flops per class                      */
+} aci_stats;
+
+/* Device memory hooks. alloc returns a device pointer of at least `bytes` bytes aligned to
+ * 256 bytes, or NULL; free releases it. Both NULL: cudaMallocAsync / cudaFreeAsync on the
+ * context stream. */
+typedef void *(*aci_alloc_fn)(size_t bytes, void *user);
+typedef void (*aci_free_fn)(void *ptr, void *user);
+
+/* Create a context on `device`, ordered on `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream). The context owns reusable scratch sized for the largest call so far.
+ * Returns ACI_OK, ACI_E_ARG (ctx NULL, exactly one hook NULL) or ACI_E_CUDA. */
+aci_status aci_create(aci_ctx **ctx, int device, void *cuda_stream,
+                      aci_alloc_fn alloc, aci_free_fn free_fn, void *user);
+
+/* Release the context and its scratch. Outputs not yet released stay valid only if they
+ * were allocated by the caller's hooks and the caller keeps the memory. NULL is a no-op. */
+void aci_destroy(aci_ctx *ctx);
+
+/* Message of the last error on this context ("" if none). Valid until the next call. */
+const char *aci_last_error(const aci_ctx *ctx);
+
+/* Fill `opts` with defaults: relative tol, 20 sweeps, full pivot search, FP64, seed 0,
+ * random initial guess, device output. */
+void aci_opts_default(aci_opts *opts);
+
+/* y ~ f(a, b) by ACI (Algorithm 1 with Algorithms 2-5, Sec. 2.6): CI-canonicalise the
+ * initial guess right to left, then alternate left-to-right and right-to-left sweeps of
+ * local updates at bonds (l, l+1). Each update forms Pi^n = L^n X^n_l X^n_{l+1} R^n
+ * (Eq. (pifromframes)), applies f entrywise, factorises Pi by the rank-revealing LU of
+ * Algorithm 2 with tolerance tau and rank cap max_rank, and updates the frames
+ * (Algorithm 5). Stops when no bond grew and the largest error estimate is <= tau, or
+ * when an iteration is a fixed point of the index sets, or after max_sweeps.
+ *  a, b      inputs (b may be NULL for ACI_OP_ABS2_MUL); same L, d and dtype.
+ *  tol       >= 0; relative to max|Pi| by default (see aci_opts.tol_kind).
+ *  max_rank  >= 1; the output ranks stay <= max_rank.
+ *  out       filled on success; the cores are library-owned until aci_tt_release().
+ * The call returns after the result is complete (one host sync per sweep). */
+aci_status aci_elementwise(aci_ctx *ctx, const aci_tt *a, const aci_tt *b, aci_op op,
+                           double tol, int32_t max_rank, aci_tt *out);
+
+/* As aci_elementwise, with explicit options (opts may be NULL for defaults) and optional
+ * diagnostics (stats may be NULL). */
+aci_status aci_elementwise_ex(aci_ctx *ctx, const aci_tt *a, const aci_tt *b, aci_op op,
+                              double tol, int32_t max_rank, const aci_opts *opts,
+                              aci_tt *out, aci_stats *stats);
+
+/* Free the library-owned parts of an output TT and zero the struct. */
+aci_status aci_tt_release(aci_ctx *ctx, aci_tt *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACI_H */

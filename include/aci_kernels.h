@@ -1,0 +1,74 @@
+/*
+ * aci_kernels.h - step-level entry points of the ACI library.
+ *
+ * Each call runs one step of the ACI hot path on device buffers the caller owns, in the
+ * same kernels aci_elementwise() uses, so that every step can be checked on its own.
+ * All matrices are row-major and contiguous unless noted; all pointers are device
+ * pointers on the context's device unless noted "host". Calls are ordered on the
+ * context stream and return after the stream has synchronised (results are ready).
+ * Status codes and error reporting are those of aci.h.
+ */
+#ifndef ACI_KERNELS_H
+#define ACI_KERNELS_H
+
+#include "aci.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Frame half-product (Algorithm 5 before truncation; Sec. 2.5, Eq. (framesrecursive)):
+ *   C[i, j] = sum_k A[arows[i], k] * B[k, bcols[j]],  i < M, j < N, k < K.
+ * A has leading dimension lda (>= K), B has leading dimension ldb. arows (length M) and
+ * bcols (length N) are optional device int32 gathers; NULL means the identity.
+ * Truncating rows to I (left frame) or columns to J (right frame) is this gather applied
+ * by the consumer. dtype is ACI_R64 or ACI_C128. C is M x N, ldc = N. */
+aci_status aci_k_frame_gemm(aci_ctx *ctx, int32_t dtype, const void *A, const int32_t *arows,
+                            int32_t M, int32_t K, int32_t lda, const void *B,
+                            const int32_t *bcols, int32_t N, int32_t ldb, void *C);
+
+/* Pi-block evaluation (Eq. (pifromframes) and Eq. (localupdate), Algorithm 1):
+ *   Pi = f(A^0 B^0, ..., A^{nprod-1} B^{nprod-1})  entrywise, Pi is M x N.
+ * A^n is M x K[n] (lda = K[n]), B^n is K[n] x N (ldb = N). nprod is 1 or 2 (2 unless
+ * op.kind == ACI_OP_ABS2_MUL). K is a host array. *maxabs (host, may be NULL) receives
+ * max |Pi| (|z| = sqrt(re^2 + im^2) for complex). */
+aci_status aci_k_pi_block(aci_ctx *ctx, int32_t dtype, int32_t nprod, const void *const *A,
+                          const void *const *B, int32_t M, int32_t N, const int32_t *K,
+                          aci_op op, void *Pi, double *maxabs);
+
+/* Rank-revealing LU with full pivot search (Algorithm 2, its garbles read as: the second
+ * swap exchanges J_j; the loop stops before accepting a pivot; L and U are unit
+ * triangular): greedy argmax |S| over the unused rows and columns, ties to the lowest
+ * row * n + col, |z|^2 = re*re + im*im for complex (no fused multiply-add),
+ * Schur-complement update, stop before a pivot with |pivot| <= tau or after chimax
+ * pivots (at least one pivot is always taken).
+ *  Min       m x n row-major input, not modified.
+ *  piv_rows, piv_cols  [min(m,n,chimax)] int32 pivot positions in pivot order.
+ *  D         [min(m,n,chimax)] pivots.
+ *  L         m x kcap column-major (column p contiguous, kcap = min(m,n,chimax)), unit lower
+ *            triangular in pivot order: L[r,p] = S_p[r,j_p] / D[p], 0 on rows pivoted before p.
+ *  U         kcap x n row-major, unit upper triangular in pivot order.
+ *  k_out, eps_out  host: rank and error estimate (magnitude of the first rejected pivot,
+ *            0 when every row or column was used). L and U may be NULL. */
+aci_status aci_k_prrlu(aci_ctx *ctx, int32_t dtype, const void *Min, int32_t m, int32_t n,
+                       double tau, int32_t chimax, int32_t *piv_rows, int32_t *piv_cols,
+                       void *D, void *L, void *U, int32_t *k_out, double *eps_out);
+
+/* Random initial guess Y^init (Algorithm 1 input; Sec. 2.6): fills cores[s]
+ * (rank[s] x d[s] x rank[s+1]) with SplitMix64 uniforms in [-1, 1): real entry e of the
+ * concatenated cores uses counter e, complex entry e uses 2e (re) and 2e+1 (im).
+ * d, rank and cores are host arrays; the cores are device buffers. */
+aci_status aci_k_tt_random(aci_ctx *ctx, int32_t dtype, uint64_t seed, int32_t L,
+                           const int32_t *d, const int64_t *rank, void *const *cores);
+
+/* Output assembly of one site (CI-canonical form, Eq. (ycicanonical) with
+ * Y_l = T_l P_l^-1, Sec. 2.5): Y = T P^-1 with P = L_I D U_J given by its unit lower
+ * factor LI (k x k, row-major), pivots D (k) and unit upper factor UJ (k x k, row-major).
+ * T and Y are R x k row-major; D[p] == 0 is read as D^-1 = 0. */
+aci_status aci_k_apply_pinv(aci_ctx *ctx, int32_t dtype, const void *T, int32_t R, int32_t k,
+                            const void *LI, const void *D, const void *UJ, void *Y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACI_KERNELS_H */

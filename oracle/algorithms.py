@@ -9,7 +9,7 @@ Index sets are kept as lists of multi-index tuples, exactly as defined in Sec. 2
 I_s holds tuples (sigma_0..sigma_s) and J_s holds tuples (sigma_s..sigma_{L-1}).
 Frames are rebuilt from the index sets with Algorithm 5 at every step (no caching).
 
-Readings of places where the paper is silent or garbled (each is listed in the design doc):
+Readings of places where the paper is silent or garbled:
   R1  tol is relative by default: tau = tol * S, S the running max |Pi| over all Pi
       blocks formed so far in the call; tol_kind="abs" gives Alg. 1's absolute tau.
       The initial-guess CI uses tau = tol * max|M| of its own matrix (or tol for "abs").
@@ -34,7 +34,7 @@ Readings of places where the paper is silent or garbled (each is listed in DESIG
       initial CI for the first). A second stop: an iteration that reproduces every J
       set of the previous one is a fixed point (the next sweep would repeat it exactly).
   R9  Y^init is the counter-based SplitMix64 TT of oracle.rng with ranks
-      min(chi_hat, min_n r^n_s), unless the caller passes one.
+      min(chi_hat, min_n r^n_s, prod_{t<s} d_t, prod_{t>=s} d_t), unless the caller passes one.
 
 Parity pins (tests/test_oracle_*.py): LDU against an independent complete-pivoting LU
 and brute-force residual identities; CI factors against exact interpolation on the
@@ -229,12 +229,13 @@ def pi_tensor(Lf, X1, X2, Rf):
 # ---------------------------------------------------------------- Algorithm 1: ACI
 
 def init_guess(inputs, chimax: int, seed: int, complex_values: bool):
-    """R9: counter-based random TT with bonds min(chi_hat, min_n r^n_s)."""
+    """R9: counter-based random TT with bonds min(chi_hat, min_n r^n_s, prod_{t<s} d_t, prod_{t>=s} d_t)."""
     L = len(inputs[0])
     dims = [c.shape[1] for c in inputs[0]]
     ranks = [1]
     for s in range(1, L):
-        ranks.append(min([chimax] + [int(x[s].shape[0]) for x in inputs]))
+        full = min(int(np.prod(dims[:s], dtype=float)), int(np.prod(dims[s:], dtype=float)))
+        ranks.append(min([chimax, full] + [int(x[s].shape[0]) for x in inputs]))
     ranks.append(1)
     return random_tt_counter(seed, ranks, dims, complex_values)
 

@@ -1,0 +1,1104 @@
+// Host driver of the ACI sweep (Algorithm 1) and the C ABI declared in include/aci.h and
+// include/aci_kernels.h. Every arithmetic step runs in the library's kernels; the host only
+// lays out buffers, enqueues launches on the context stream, and reads one small flag
+// record per sweep (the stop test of Algorithm 1).
+//
+// Data layout in HBM for one call (0-based sites s = 0..L-1, bond b joins sites b and b+1):
+//   chi[0..L]      output ranks (device), chi[b+1] = |I_b| = |J_{b+1}|, set by bond b's pivots
+//   LX[n][s]       L^n_{s-1} X^n_s, (chi[s] d_s) x r^n_{s+1} row-major; LX[n][0] aliases X^n_0
+//   XR[n][s]       X^n_s R^n_{s+1}, r^n_s x (d_s chi[s+1]) row-major; XR[n][L-1] aliases X^n_{L-1}
+//   Pi[b]          f(LX[.][b] XR[.][b+1]), (chi[b] d_b) x (d_{b+1} chi[b+2]) row-major
+//   prow/pcol[b]   bond b's pivots (positions in Pi[b]); D[b], Lm[b] (col-major), Um[b] (row-major)
+// The frames L^n_b = rows prow[b] of LX[n][b] and R^n_{s} = columns pcol[s-1] of XR[n][s] are
+// never materialised: the next contraction gathers them on load. LX[.][b] from a left-to-right
+// sweep is reused by the following right-to-left sweep at the same bond, and XR[.][b+1] from a
+// right-to-left sweep by the next left-to-right sweep (their frames have not changed).
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/aci.h"
+#include "../../include/aci_kernels.h"
+#include "aci_internal.h"
+
+using aci::cplx;
+using aci::DimE;
+using aci::dimc;
+using aci::dimr;
+
+struct aci_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    aci_alloc_fn alloc = nullptr;
+    aci_free_fn free_fn = nullptr;
+    void* user = nullptr;
+    std::string err;
+    int num_sms = 0;
+    unsigned long long epoch = 1;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    aci::IterFlags* hflags = nullptr;  // pinned
+    long long launches = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> evfree;  // reusable events for per-kernel timing
+    std::vector<cudaEvent_t> evall;
+};
+
+namespace {
+
+struct Fail {
+    aci_status st;
+};
+
+void fail(aci_ctx* ctx, aci_status st, const std::string& msg) {
+    ctx->err = msg;
+    throw Fail{st};
+}
+
+void ck(aci_ctx* ctx, cudaError_t e, const char* what) {
+    if (e != cudaSuccess) fail(ctx, ACI_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* dev_alloc(aci_ctx* ctx, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (ctx->alloc) {
+        p = ctx->alloc(bytes, ctx->user);
+    } else {
+        if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess) p = nullptr;
+    }
+    if (!p) fail(ctx, ACI_E_ALLOC, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    return p;
+}
+
+void dev_free(aci_ctx* ctx, void* p) {
+    if (!p) return;
+    if (ctx->free_fn) ctx->free_fn(p, ctx->user);
+    else cudaFreeAsync(p, ctx->stream);
+}
+
+// Grow the context workspace to at least `bytes`.
+char* workspace(aci_ctx* ctx, size_t bytes) {
+    if (bytes > ctx->ws_bytes) {
+        if (ctx->ws) dev_free(ctx, ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+        const size_t want = bytes + bytes / 8;
+        ctx->ws = dev_alloc(ctx, want);
+        ctx->ws_bytes = want;
+    }
+    return static_cast<char*>(ctx->ws);
+}
+
+// Bump allocator over the workspace; the same layout routine runs once to size, once to carve.
+struct Carver {
+    char* base = nullptr;
+    size_t off = 0;
+    template <class U> U* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        U* p = base ? reinterpret_cast<U*>(base + off) : nullptr;
+        off += count * sizeof(U);
+        return p;
+    }
+};
+
+void note_launch(aci_ctx* ctx, const char* what) {
+    ctx->launches++;
+    ck(ctx, cudaGetLastError(), what);
+}
+
+long long sat_mul(long long a, long long b, long long cap) {
+    if (a >= cap || b >= cap) return cap;
+    long long v = a * b;
+    return v > cap ? cap : v;
+}
+
+template <class T>
+aci::OpParams<T> make_op(const aci_op& op);
+template <>
+aci::OpParams<double> make_op<double>(const aci_op& op) {
+    aci::OpParams<double> p;
+    p.kind = op.kind;
+    for (int i = 0; i < 4; ++i) p.c[i] = op.c[i][0];
+    return p;
+}
+template <>
+aci::OpParams<cplx> make_op<cplx>(const aci_op& op) {
+    aci::OpParams<cplx> p;
+    p.kind = op.kind;
+    for (int i = 0; i < 4; ++i) p.c[i] = aci::mkc(op.c[i][0], op.c[i][1]);
+    return p;
+}
+
+// ------------------------------------------------------------------------------------------
+// One ACI call (Algorithm 1) for scalar type T.
+template <class T>
+struct Run {
+    aci_ctx* ctx;
+    cudaStream_t st;
+    int L = 0, N = 0, chimax = 0, maxit = 20, rel = 1, prof = 0;
+    // per-kernel-class accounting (aci_kernel_class)
+    double kms[4] = {0, 0, 0, 0};
+    long long kcount[4] = {0, 0, 0, 0};
+    double* kflops = nullptr;  // device [4]
+    struct Pend {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pend> pend;
+
+    cudaEvent_t get_event() {
+        if (ctx->evfree.empty()) {
+            cudaEvent_t e;
+            ck(ctx, cudaEventCreate(&e), "cudaEventCreate");
+            ctx->evall.push_back(e);
+            return e;
+        }
+        cudaEvent_t e = ctx->evfree.back();
+        ctx->evfree.pop_back();
+        return e;
+    }
+    cudaEvent_t pre(int) {
+        if (!prof) return nullptr;
+        cudaEvent_t e = get_event();
+        ck(ctx, cudaEventRecord(e, st), "event");
+        return e;
+    }
+    void post(int cls, cudaEvent_t a, const char* what) {
+        note_launch(ctx, what);
+        kcount[cls]++;
+        if (!prof) return;
+        cudaEvent_t b = get_event();
+        ck(ctx, cudaEventRecord(b, st), "event");
+        pend.push_back({cls, a, b});
+    }
+    // After a stream sync: fold the finished event pairs into kms.
+    void harvest() {
+        for (auto& q : pend) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) kms[q.cls] += ms;
+            ctx->evfree.push_back(q.a);
+            ctx->evfree.push_back(q.b);
+        }
+        pend.clear();
+    }
+    double* flops_of(int cls) { return prof ? kflops + cls : nullptr; }
+    double tol = 0;
+    uint64_t seed = 0;
+    aci::OpParams<T> op;
+    std::vector<int> d;                    // [L]
+    std::vector<std::vector<int>> r;       // r[n][0..L] input ranks
+    std::vector<int> cap, ry;              // [L+1]
+    std::vector<int> mcap, ncap, kcap;     // per bond
+    bool host_in = false;
+    const aci_tt* in[2] = {nullptr, nullptr};
+    const aci_tt* init = nullptr;
+
+    // device buffers
+    std::vector<const T*> Xv[2];
+    std::vector<T*> Xcopy[2];
+    std::vector<T*> LX[2], XR[2], Yinit, Ysc, Pi, D, Lm, Um;
+    std::vector<int*> prow, pcol, jprev;
+    T* Minit[2] = {nullptr, nullptr};
+    int *chi = nullptr, *chi_prev = nullptr, *dd = nullptr, *err = nullptr;
+    double *eps_lr = nullptr, *eps_rl = nullptr, *eps_junk = nullptr;
+    unsigned long long *smax = nullptr, *initmax = nullptr;
+    aci::IterFlags* flags = nullptr;
+    T* ones = nullptr;
+    T* W = nullptr;
+    aci::PivRec* rec = nullptr;
+    T* slots = nullptr;
+    int Gmax = 1;
+    size_t wcap = 0;
+    int mmax_all = 1;
+    aci::BondBuf<T>* bonds_dev = nullptr;
+    T** Yptr_dev = nullptr;
+    int** pcol_dev = nullptr;
+    int** jprev_dev = nullptr;
+
+    const T* Xp(int n, int s) const { return Xv[n][s]; }
+
+    void layout(Carver& c) {
+        for (int n = 0; n < N; ++n) {
+            Xcopy[n].assign(L, nullptr);
+            if (host_in)
+                for (int s = 0; s < L; ++s)
+                    Xcopy[n][s] = c.take<T>((size_t)r[n][s] * d[s] * r[n][s + 1]);
+            LX[n].assign(L, nullptr);
+            XR[n].assign(L, nullptr);
+            for (int s = 1; s < L; ++s) LX[n][s] = c.take<T>((size_t)cap[s] * d[s] * r[n][s + 1]);
+            for (int s = 0; s + 1 < L; ++s) XR[n][s] = c.take<T>((size_t)r[n][s] * d[s] * cap[s + 1]);
+        }
+        const int nb = std::max(L - 1, 0);
+        Pi.assign(nb, nullptr);
+        D.assign(nb, nullptr);
+        Lm.assign(nb, nullptr);
+        Um.assign(nb, nullptr);
+        prow.assign(nb, nullptr);
+        pcol.assign(nb, nullptr);
+        jprev.assign(nb, nullptr);
+        for (int b = 0; b < nb; ++b) {
+            Pi[b] = c.take<T>((size_t)mcap[b] * ncap[b]);
+            D[b] = c.take<T>(kcap[b]);
+            Lm[b] = c.take<T>((size_t)mcap[b] * kcap[b]);
+            Um[b] = c.take<T>((size_t)kcap[b] * ncap[b]);
+            prow[b] = c.take<int>(kcap[b]);
+            pcol[b] = c.take<int>(kcap[b]);
+            jprev[b] = c.take<int>(kcap[b]);
+        }
+        Yinit.assign(L, nullptr);
+        Ysc.assign(L, nullptr);
+        size_t minit = 1;
+        for (int s = 0; s < L; ++s) {
+            Yinit[s] = c.take<T>((size_t)ry[s] * d[s] * ry[s + 1]);
+            Ysc[s] = c.take<T>((size_t)cap[s] * d[s] * cap[s + 1]);
+            minit = std::max(minit, (size_t)ry[s] * d[s] * cap[s + 1]);
+        }
+        Minit[0] = c.take<T>(minit);
+        Minit[1] = c.take<T>(minit);
+        chi = c.take<int>(L + 1);
+        chi_prev = c.take<int>(L + 1);
+        dd = c.take<int>(L);
+        err = c.take<int>(1);
+        eps_lr = c.take<double>(std::max(nb, 1));
+        eps_rl = c.take<double>(std::max(nb, 1));
+        eps_junk = c.take<double>(1);
+        kflops = c.take<double>(4);
+        smax = c.take<unsigned long long>(1);
+        initmax = c.take<unsigned long long>(1);
+        flags = c.take<aci::IterFlags>(1);
+        ones = c.take<T>(1);
+        W = c.take<T>(wcap);
+        rec = c.take<aci::PivRec>(2 * (size_t)Gmax);
+        slots = c.take<T>(2 * (size_t)Gmax * mmax_all);
+        bonds_dev = c.take<aci::BondBuf<T>>(std::max(nb, 1));
+        Yptr_dev = c.take<T*>(L);
+        pcol_dev = c.take<int*>(std::max(nb, 1));
+        jprev_dev = c.take<int*>(std::max(nb, 1));
+    }
+
+    void plan_sizes() {
+        cap.assign(L + 1, 1);
+        const long long big = 1LL << 40;
+        for (int s = 1; s < L; ++s) {
+            long long pl = 1, pr = 1;
+            for (int t = 0; t < s; ++t) pl = sat_mul(pl, d[t], big);
+            for (int t = s; t < L; ++t) pr = sat_mul(pr, d[t], big);
+            cap[s] = (int)std::min<long long>({(long long)chimax, pl, pr});
+        }
+        ry.assign(L + 1, 1);
+        for (int s = 1; s < L; ++s) {
+            int v = cap[s];
+            for (int n = 0; n < N; ++n) v = std::min(v, r[n][s]);
+            if (init) {
+                if (init->rank[s] > cap[s])
+                    fail(ctx, ACI_E_SHAPE, "init rank exceeds min(max_rank, prod d left, prod d right)");
+                v = (int)init->rank[s];
+            }
+            ry[s] = v;
+        }
+        const int nb = std::max(L - 1, 0);
+        mcap.assign(nb, 0);
+        ncap.assign(nb, 0);
+        kcap.assign(nb, 0);
+        wcap = 1;
+        mmax_all = 1;
+        Gmax = 1;
+        for (int b = 0; b < nb; ++b) {
+            mcap[b] = cap[b] * d[b];
+            ncap[b] = d[b + 1] * cap[b + 2];
+            kcap[b] = cap[b + 1];
+            wcap = std::max(wcap, (size_t)mcap[b] * ncap[b]);
+            mmax_all = std::max(mmax_all, mcap[b]);
+            Gmax = std::max(Gmax, aci::prrlu_grid(ncap[b], ctx->num_sms));
+            if ((long long)mcap[b] * ncap[b] >= (1LL << 31))
+                fail(ctx, ACI_E_SHAPE, "a Pi block would exceed 2^31 entries");
+        }
+        for (int s = 1; s < L; ++s) {
+            const int m = ry[s], n = d[s] * cap[s + 1];
+            wcap = std::max(wcap, (size_t)m * n);
+            mmax_all = std::max(mmax_all, m);
+            Gmax = std::max(Gmax, aci::prrlu_grid(n, ctx->num_sms));
+        }
+    }
+
+    // ---------------------------------------------------------------- launches
+    void gemm(aci::GemmArgs<T>& g, int Mmax, int Nmax, const char* what, int cls) {
+        g.chi = chi;
+        g.flops = flops_of(cls);
+        cudaEvent_t e = pre(cls);
+        aci::launch_gemm<T>(g, Mmax, Nmax, st);
+        post(cls, e, what);
+    }
+
+    aci::GemmArgs<T> gemm_base() {
+        aci::GemmArgs<T> g;
+        std::memset(&g, 0, sizeof(g));
+        g.op = op;
+        return g;
+    }
+
+    void prrlu(const T* Min, DimE m, DimE n, int mm, int nn, int out_idx, int b_store, bool with_lu,
+               double* eps_out, const unsigned long long* S) {
+        aci::PrrluArgs<T> a;
+        std::memset(&a, 0, sizeof(a));
+        a.Min = Min;
+        a.m = m;
+        a.n = n;
+        a.chi = chi;
+        a.chimax = chimax;
+        a.out_chi_idx = out_idx;
+        a.eps_out = eps_out;
+        a.piv_rows = prow[b_store];
+        a.piv_cols = pcol[b_store];
+        a.D = D[b_store];
+        if (with_lu) {
+            a.L = Lm[b_store];
+            a.Lld = mcap[b_store];
+            a.U = Um[b_store];
+            a.Uld = ncap[b_store];
+        }
+        a.tol = tol;
+        a.rel = rel;
+        a.smax = S;
+        a.W = W;
+        a.rec = rec;
+        a.slots = slots;
+        a.mmax = mm;
+        a.nmax = nn;
+        a.epoch = ctx->epoch++;
+        a.err = err;
+        a.flops = flops_of(ACI_KCLASS_PIVOT);
+        const int G = aci::prrlu_grid(nn, ctx->num_sms);
+        cudaEvent_t e = pre(ACI_KCLASS_PIVOT);
+        ck(ctx, aci::launch_prrlu<T>(a, G, st), "prrlu launch");
+        post(ACI_KCLASS_PIVOT, e, "prrlu");
+    }
+
+    // Pi[b] = f(LX[.][b] XR[.][b+1]) with the running max |Pi| (Eq. (pifromframes)).
+    void pi_block(int b) {
+        aci::GemmArgs<T> g = gemm_base();
+        g.combine = 1;
+        g.nprod = N;
+        for (int n = 0; n < N; ++n) {
+            g.A[n] = (b == 0) ? Xp(n, 0) : LX[n][b];
+            g.B[n] = (b + 1 == L - 1) ? Xp(n, L - 1) : XR[n][b + 1];
+            g.K[n] = dimc(r[n][b + 1]);
+            g.lda[n] = dimc(r[n][b + 1]);
+            g.ldb[n] = dimr(d[b + 1], b + 2);
+        }
+        g.M[0] = dimr(d[b], b);
+        g.N[0] = dimr(d[b + 1], b + 2);
+        g.C[0] = Pi[b];
+        g.smax = smax;
+        gemm(g, mcap[b], ncap[b], "pi_block", ACI_KCLASS_PI);
+    }
+
+    // LX[n][b] = rows prow[b-1] of LX[n][b-1], times X^n_b (Leftframe of Algorithm 5).
+    void left_half(int b) {
+        if (b == 0) return;
+        aci::GemmArgs<T> g = gemm_base();
+        g.combine = 0;
+        g.nprod = N;
+        int nmax = 1;
+        for (int n = 0; n < N; ++n) {
+            g.A[n] = (b - 1 == 0) ? Xp(n, 0) : LX[n][b - 1];
+            g.B[n] = Xp(n, b);
+            g.C[n] = LX[n][b];
+            g.M[n] = dimr(1, b);
+            g.N[n] = dimc(d[b] * r[n][b + 1]);
+            g.K[n] = dimc(r[n][b]);
+            g.lda[n] = dimc(r[n][b]);
+            g.ldb[n] = dimc(d[b] * r[n][b + 1]);
+            nmax = std::max(nmax, d[b] * r[n][b + 1]);
+        }
+        g.arow = prow[b - 1];
+        gemm(g, cap[b], nmax, "left_half", ACI_KCLASS_FRAME);
+    }
+
+    // XR[n][s] = X^n_s times columns pcol[s] of XR[n][s+1] (Rightframe of Algorithm 5).
+    void right_half(int s) {
+        if (s >= L - 1) return;
+        aci::GemmArgs<T> g = gemm_base();
+        g.combine = 0;
+        g.nprod = N;
+        int mmax = 1;
+        for (int n = 0; n < N; ++n) {
+            g.A[n] = Xp(n, s);
+            g.B[n] = (s + 1 == L - 1) ? Xp(n, L - 1) : XR[n][s + 1];
+            g.C[n] = XR[n][s];
+            g.M[n] = dimc(r[n][s] * d[s]);
+            g.N[n] = dimr(1, s + 1);
+            g.K[n] = dimc(r[n][s + 1]);
+            g.lda[n] = dimc(r[n][s + 1]);
+            g.ldb[n] = dimr(d[s + 1], s + 2);
+            mmax = std::max(mmax, r[n][s] * d[s]);
+        }
+        g.bcol = pcol[s];
+        gemm(g, mmax, cap[s + 1], "right_half", ACI_KCLASS_FRAME);
+    }
+
+    // ---------------------------------------------------------------- Algorithm 1
+    aci_status run(aci_tt* out, aci_stats* stats, int out_memory) {
+        plan_sizes();
+        Carver sizer;
+        layout(sizer);
+        Carver carver;
+        carver.base = workspace(ctx, sizer.off);
+        layout(carver);
+        for (int n = 0; n < N; ++n) {
+            Xv[n].assign(L, nullptr);
+            for (int s = 0; s < L; ++s) {
+                const size_t cnt = (size_t)r[n][s] * d[s] * r[n][s + 1];
+                if (host_in) {
+                    ck(ctx, cudaMemcpyAsync(Xcopy[n][s], in[n]->core[s], cnt * sizeof(T), cudaMemcpyHostToDevice, st), "copy input");
+                    Xv[n][s] = Xcopy[n][s];
+                } else {
+                    Xv[n][s] = static_cast<const T*>(in[n]->core[s]);
+                }
+            }
+        }
+        ck(ctx, cudaEventRecord(ctx->ev0, st), "event");
+        const long long launches0 = ctx->launches;
+        const int nb = L - 1;
+
+        // constants and per-call state
+        std::vector<int> chi_h(L + 1, 0);
+        chi_h[0] = 1;
+        chi_h[L] = 1;
+        ck(ctx, cudaMemcpyAsync(chi, chi_h.data(), sizeof(int) * (L + 1), cudaMemcpyHostToDevice, st), "init chi");
+        ck(ctx, cudaMemcpyAsync(dd, d.data(), sizeof(int) * L, cudaMemcpyHostToDevice, st), "init d");
+        ck(ctx, cudaMemsetAsync(err, 0, sizeof(int), st), "memset");
+        ck(ctx, cudaMemsetAsync(smax, 0, sizeof(unsigned long long), st), "memset");
+        ck(ctx, cudaMemsetAsync(kflops, 0, 4 * sizeof(double), st), "memset");
+        T one_h;
+        std::memset(&one_h, 0, sizeof(T));
+        *reinterpret_cast<double*>(&one_h) = 1.0;
+        ck(ctx, cudaMemcpyAsync(ones, &one_h, sizeof(T), cudaMemcpyHostToDevice, st), "ones");
+        if (nb > 0) {
+            std::vector<aci::BondBuf<T>> bb(nb);
+            std::vector<int*> pc(nb), jp(nb);
+            for (int b = 0; b < nb; ++b) {
+                bb[b].Pi = Pi[b];
+                bb[b].prow = prow[b];
+                bb[b].pcol = pcol[b];
+                bb[b].D = D[b];
+                bb[b].Lm = Lm[b];
+                bb[b].Um = Um[b];
+                bb[b].Lld = mcap[b];
+                bb[b].Uld = ncap[b];
+                pc[b] = pcol[b];
+                jp[b] = jprev[b];
+            }
+            ck(ctx, cudaMemcpyAsync(bonds_dev, bb.data(), sizeof(bb[0]) * nb, cudaMemcpyHostToDevice, st), "bonds");
+            ck(ctx, cudaMemcpyAsync(pcol_dev, pc.data(), sizeof(int*) * nb, cudaMemcpyHostToDevice, st), "pcol");
+            ck(ctx, cudaMemcpyAsync(jprev_dev, jp.data(), sizeof(int*) * nb, cudaMemcpyHostToDevice, st), "jprev");
+            ck(ctx, cudaMemcpyAsync(Yptr_dev, Ysc.data(), sizeof(T*) * L, cudaMemcpyHostToDevice, st), "Yptr");
+        }
+
+        if (L == 1) {  // no bond: y = f(x) on the single site
+            aci::GemmArgs<T> g = gemm_base();
+            g.combine = 1;
+            g.nprod = N;
+            for (int n = 0; n < N; ++n) {
+                g.A[n] = Xp(n, 0);
+                g.B[n] = ones;
+                g.K[n] = dimc(1);
+                g.lda[n] = dimc(1);
+                g.ldb[n] = dimc(1);
+            }
+            g.M[0] = dimc(d[0]);
+            g.N[0] = dimc(1);
+            g.C[0] = Ysc[0];
+            g.smax = smax;
+            gemm(g, d[0], 1, "single_site", ACI_KCLASS_PI);
+            return finish(out, stats, out_memory, 0, 1, 0, launches0);
+        }
+
+        // ---- initial guess: counter-based random TT, or the caller's warm start
+        if (init) {
+            for (int s = 0; s < L; ++s) {
+                const size_t cnt = (size_t)ry[s] * d[s] * ry[s + 1];
+                const cudaMemcpyKind kind = init->memory == ACI_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+                ck(ctx, cudaMemcpyAsync(Yinit[s], init->core[s], cnt * sizeof(T), kind, st), "copy init");
+            }
+        } else {
+            std::vector<long long> off(L), cnt(L);
+            long long o = 0;
+            for (int s = 0; s < L; ++s) {
+                cnt[s] = (long long)ry[s] * d[s] * ry[s + 1];
+                off[s] = o;
+                o += cnt[s];
+            }
+            cudaEvent_t e = pre(ACI_KCLASS_OTHER);
+            aci::launch_tt_random<T>(seed, L, off.data(), cnt.data(), Yinit.data(), st);
+            ctx->launches += L - 1;
+            kcount[ACI_KCLASS_OTHER] += L - 1;
+            post(ACI_KCLASS_OTHER, e, "tt_random");
+        }
+
+        // ---- CI-canonicalise Y^init right to left; build the right frames (Algorithm 1)
+        for (int s = L - 1; s >= 1; --s) {
+            T* Ms = Minit[s & 1];
+            ck(ctx, cudaMemsetAsync(initmax, 0, sizeof(unsigned long long), st), "memset");
+            aci::GemmArgs<T> g = gemm_base();
+            g.combine = 0;
+            g.nprod = 1;
+            g.A[0] = Yinit[s];
+            g.C[0] = Ms;
+            g.M[0] = dimc(ry[s] * d[s]);
+            g.N[0] = dimr(1, s + 1);
+            g.K[0] = dimc(ry[s + 1]);
+            g.lda[0] = dimc(ry[s + 1]);
+            if (s == L - 1) {
+                g.B[0] = ones;
+                g.ldb[0] = dimc(1);
+            } else {
+                g.B[0] = Minit[(s + 1) & 1];
+                g.ldb[0] = dimr(d[s + 1], s + 2);
+                g.bcol = pcol[s];
+            }
+            g.smax = initmax;
+            gemm(g, ry[s] * d[s], cap[s + 1], "init_gemm", ACI_KCLASS_OTHER);
+            prrlu(Ms, dimc(ry[s]), dimr(d[s], s + 1), ry[s], d[s] * cap[s + 1], s, s - 1, false,
+                  eps_junk, initmax);
+            right_half(s);
+        }
+        {
+            cudaEvent_t e = pre(ACI_KCLASS_OTHER);
+            aci::launch_iter_check(L, chi, chi_prev, pcol_dev, jprev_dev, eps_lr, eps_rl, smax, err, flags, 1, st);
+            post(ACI_KCLASS_OTHER, e, "iter_snapshot");
+        }
+
+        // ---- sweeps
+        int it = 0, converged = 0, fixed = 0;
+        aci::IterFlags fl;
+        std::memset(&fl, 0, sizeof(fl));
+        for (it = 1; it <= maxit; ++it) {
+            for (int b = 0; b < nb; ++b) {  // left to right, CI "right"
+                left_half(b);
+                pi_block(b);
+                prrlu(Pi[b], dimr(d[b], b), dimr(d[b + 1], b + 2), mcap[b], ncap[b], b + 1, b, false,
+                      eps_lr + b, smax);
+            }
+            for (int b = nb - 1; b >= 0; --b) {  // right to left, CI "left"
+                right_half(b + 1);
+                pi_block(b);
+                prrlu(Pi[b], dimr(d[b], b), dimr(d[b + 1], b + 2), mcap[b], ncap[b], b + 1, b, true,
+                      eps_rl + b, smax);
+            }
+            cudaEvent_t e = pre(ACI_KCLASS_OTHER);
+            aci::launch_iter_check(L, chi, chi_prev, pcol_dev, jprev_dev, eps_lr, eps_rl, smax, err, flags, 0, st);
+            post(ACI_KCLASS_OTHER, e, "iter_check");
+            ck(ctx, cudaMemcpyAsync(ctx->hflags, flags, sizeof(aci::IterFlags), cudaMemcpyDeviceToHost, st), "flags");
+            ck(ctx, cudaStreamSynchronize(st), "sweep");
+            fl = *ctx->hflags;
+            harvest();
+            if (fl.err & aci::DEVERR_TIMEOUT) fail(ctx, ACI_E_TIMEOUT, "a device-side wait in the pivot search timed out");
+            if ((fl.err & aci::DEVERR_NUMERIC) || !(fl.S < INFINITY))
+                fail(ctx, ACI_E_NUMERIC, "a non-finite value reached the pivot search");
+            const double tau = rel ? tol * fl.S : tol;
+            if (!fl.grew && fl.emax <= tau) { converged = 1; break; }
+            if (fl.fixed) { fixed = 1; break; }
+        }
+        if (it > maxit) it = maxit;
+
+        // ---- output: Y_s = T_s P_s^-1 (CI-canonical form)
+        aci::AssembleArgs<T> aa;
+        aa.L = L;
+        aa.chi = chi;
+        aa.d = dd;
+        aa.bonds = bonds_dev;
+        aa.Y = Yptr_dev;
+        int Rmax = 1;
+        for (int s = 0; s < L; ++s) Rmax = std::max(Rmax, cap[s] * d[s]);
+        cudaEvent_t e = pre(ACI_KCLASS_OTHER);
+        aci::launch_assemble<T>(aa, Rmax, st);
+        post(ACI_KCLASS_OTHER, e, "assemble");
+        return finish(out, stats, out_memory, it, converged, fixed, launches0, &fl);
+    }
+
+    aci_status finish(aci_tt* out, aci_stats* stats, int out_memory, int it, int converged, int fixed,
+                      long long launches0, const aci::IterFlags* fl = nullptr) {
+        ck(ctx, cudaEventRecord(ctx->ev1, st), "event");
+        std::vector<int> chi_h(L + 1, 1);
+        if (L > 1) ck(ctx, cudaMemcpyAsync(chi_h.data(), chi, sizeof(int) * (L + 1), cudaMemcpyDeviceToHost, st), "read chi");
+        ck(ctx, cudaStreamSynchronize(st), "finish");
+        int errflag = 0;
+        ck(ctx, cudaMemcpy(&errflag, err, sizeof(int), cudaMemcpyDeviceToHost), "read err");
+        if (errflag & aci::DEVERR_TIMEOUT) fail(ctx, ACI_E_TIMEOUT, "a device-side wait in the pivot search timed out");
+        if (errflag & aci::DEVERR_NUMERIC) fail(ctx, ACI_E_NUMERIC, "a non-finite value reached the pivot search");
+        // allocate and fill the output TT
+        int32_t* od = static_cast<int32_t*>(std::malloc(sizeof(int32_t) * L));
+        int64_t* orank = static_cast<int64_t*>(std::malloc(sizeof(int64_t) * (L + 1)));
+        void** ocore = static_cast<void**>(std::calloc(L, sizeof(void*)));
+        if (!od || !orank || !ocore) {
+            std::free(od);
+            std::free(orank);
+            std::free(ocore);
+            fail(ctx, ACI_E_ALLOC, "host allocation failed");
+        }
+        for (int s = 0; s < L; ++s) od[s] = d[s];
+        for (int s = 0; s <= L; ++s) orank[s] = chi_h[s];
+        try {
+            for (int s = 0; s < L; ++s) {
+                const size_t cnt = (size_t)orank[s] * d[s] * orank[s + 1];
+                if (out_memory == ACI_MEM_HOST) {
+                    ocore[s] = std::malloc(std::max<size_t>(cnt * sizeof(T), 1));
+                    if (!ocore[s]) fail(ctx, ACI_E_ALLOC, "host allocation failed");
+                    ck(ctx, cudaMemcpyAsync(ocore[s], Ysc[s], cnt * sizeof(T), cudaMemcpyDeviceToHost, st), "copy out");
+                } else {
+                    ocore[s] = dev_alloc(ctx, cnt * sizeof(T));
+                    ck(ctx, cudaMemcpyAsync(ocore[s], Ysc[s], cnt * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy out");
+                }
+            }
+            ck(ctx, cudaStreamSynchronize(st), "copy out");
+        } catch (Fail&) {
+            for (int s = 0; s < L; ++s) {
+                if (!ocore[s]) continue;
+                if (out_memory == ACI_MEM_HOST) std::free(ocore[s]);
+                else dev_free(ctx, ocore[s]);
+            }
+            std::free(od);
+            std::free(orank);
+            std::free(ocore);
+            throw;
+        }
+        out->L = L;
+        out->dtype = aci::dtype_id<T>::value;
+        out->memory = out_memory;
+        out->d = od;
+        out->rank = orank;
+        out->core = ocore;
+        if (stats) {
+            stats->iterations = it;
+            stats->converged = converged;
+            stats->fixed_point = fixed;
+            stats->L = L;
+            stats->scale = fl ? fl->S : 0.0;
+            stats->max_eps = fl ? fl->emax : 0.0;
+            stats->tau = fl ? (rel ? tol * fl->S : tol) : tol;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            stats->device_ms = ms;
+            stats->kernel_launches = ctx->launches - launches0;
+            harvest();
+            double fl_h[4] = {0, 0, 0, 0};
+            if (prof) ck(ctx, cudaMemcpy(fl_h, kflops, sizeof(fl_h), cudaMemcpyDeviceToHost), "flops");
+            for (int q = 0; q < 4; ++q) {
+                stats->kernel_ms[q] = kms[q];
+                stats->kernel_count[q] = kcount[q];
+                stats->kernel_flops[q] = fl_h[q];
+            }
+            if (stats->ranks)
+                for (int s = 0; s <= L; ++s) stats->ranks[s] = chi_h[s];
+            if (stats->eps && L > 1) {
+                std::vector<double> a(L - 1), b(L - 1);
+                ck(ctx, cudaMemcpy(a.data(), eps_lr, sizeof(double) * (L - 1), cudaMemcpyDeviceToHost), "eps");
+                ck(ctx, cudaMemcpy(b.data(), eps_rl, sizeof(double) * (L - 1), cudaMemcpyDeviceToHost), "eps");
+                for (int q = 0; q < L - 1; ++q) stats->eps[q] = std::max(a[q], b[q]);
+            }
+            for (int b = 0; b + 1 < L; ++b) {
+                const int k = chi_h[b + 1];
+                if (stats->pivot_rows)
+                    ck(ctx, cudaMemcpy(stats->pivot_rows + (size_t)b * chimax, prow[b], sizeof(int) * k, cudaMemcpyDeviceToHost), "pivots");
+                if (stats->pivot_cols)
+                    ck(ctx, cudaMemcpy(stats->pivot_cols + (size_t)b * chimax, pcol[b], sizeof(int) * k, cudaMemcpyDeviceToHost), "pivots");
+            }
+        }
+        return converged || fixed || L == 1 ? ACI_OK : ACI_W_NOT_CONVERGED;
+    }
+};
+
+void validate_tt(aci_ctx* ctx, const aci_tt* t, const char* name) {
+    if (!t->d || !t->rank || !t->core) fail(ctx, ACI_E_ARG, std::string(name) + ": null array");
+    if (t->L < 1) fail(ctx, ACI_E_SHAPE, std::string(name) + ": L < 1");
+    if (t->L > 4096) fail(ctx, ACI_E_SHAPE, std::string(name) + ": L > 4096");
+    if (t->dtype != ACI_R64 && t->dtype != ACI_C128) fail(ctx, ACI_E_DTYPE, std::string(name) + ": unsupported dtype");
+    if (t->memory != ACI_MEM_DEVICE && t->memory != ACI_MEM_HOST) fail(ctx, ACI_E_ARG, std::string(name) + ": bad memory kind");
+    if (t->rank[0] != 1 || t->rank[t->L] != 1) fail(ctx, ACI_E_SHAPE, std::string(name) + ": rank[0] and rank[L] must be 1");
+    for (int s = 0; s < t->L; ++s) {
+        if (t->d[s] < 1 || t->d[s] > 4096) fail(ctx, ACI_E_SHAPE, std::string(name) + ": d out of range");
+        if (t->rank[s + 1] < 1 || t->rank[s + 1] > (1 << 20)) fail(ctx, ACI_E_SHAPE, std::string(name) + ": rank out of range");
+        if (!t->core[s]) fail(ctx, ACI_E_ARG, std::string(name) + ": null core");
+    }
+}
+
+template <class T>
+aci_status run_typed(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, double tol, int32_t max_rank,
+                     const aci_opts& o, aci_tt* out, aci_stats* stats) {
+    Run<T> R;
+    R.ctx = ctx;
+    R.st = ctx->stream;
+    R.L = a->L;
+    R.N = (op.kind == ACI_OP_ABS2_MUL) ? 1 : 2;
+    R.in[0] = a;
+    R.in[1] = (R.N == 2) ? b : nullptr;
+    R.chimax = max_rank;
+    R.tol = tol;
+    R.rel = o.tol_kind == ACI_TOL_REL;
+    R.maxit = o.max_sweeps;
+    R.prof = o.profile ? 1 : 0;
+    R.seed = o.seed;
+    R.op = make_op<T>(op);
+    R.init = o.init;
+    R.host_in = a->memory == ACI_MEM_HOST;
+    R.d.assign(a->d, a->d + a->L);
+    R.r.assign(R.N, std::vector<int>(a->L + 1));
+    for (int n = 0; n < R.N; ++n)
+        for (int s = 0; s <= a->L; ++s) R.r[n][s] = (int)R.in[n]->rank[s];
+    return R.run(out, stats, o.out_memory);
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+aci_status aci_create(aci_ctx** ctx_out, int device, void* cuda_stream, aci_alloc_fn alloc, aci_free_fn free_fn,
+                      void* user) {
+    if (!ctx_out) return ACI_E_ARG;
+    *ctx_out = nullptr;
+    if ((alloc == nullptr) != (free_fn == nullptr)) return ACI_E_ARG;
+    aci_ctx* ctx = new (std::nothrow) aci_ctx();
+    if (!ctx) return ACI_E_ALLOC;
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    ctx->alloc = alloc;
+    ctx->free_fn = free_fn;
+    ctx->user = user;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMallocHost(&ctx->hflags, sizeof(aci::IterFlags)) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->hflags) cudaFreeHost(ctx->hflags);
+        delete ctx;
+        return ACI_E_CUDA;
+    }
+    *ctx_out = ctx;
+    return ACI_OK;
+}
+
+void aci_destroy(aci_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws) dev_free(ctx, ctx->ws);
+    if (!ctx->alloc) cudaStreamSynchronize(ctx->stream);
+    if (ctx->hflags) cudaFreeHost(ctx->hflags);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (cudaEvent_t e : ctx->evall) cudaEventDestroy(e);
+    delete ctx;
+}
+
+const char* aci_last_error(const aci_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void aci_opts_default(aci_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol_kind = ACI_TOL_REL;
+    o->max_sweeps = 20;
+    o->pivot_mode = ACI_PIVOT_FULL;
+    o->precision = ACI_PREC_FP64;
+    o->seed = 0;
+    o->init = nullptr;
+    o->out_memory = ACI_MEM_DEVICE;
+}
+
+aci_status aci_elementwise_ex(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, double tol, int32_t max_rank,
+                              const aci_opts* opts, aci_tt* out, aci_stats* stats) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    try {
+        if (!a || !out) fail(ctx, ACI_E_ARG, "a and out must not be NULL");
+        if (op.kind < ACI_OP_MUL || op.kind > ACI_OP_AFFINE) fail(ctx, ACI_E_ARG, "unknown op kind");
+        if (!(tol >= 0.0) || !(tol < INFINITY)) fail(ctx, ACI_E_ARG, "tol must be finite and >= 0");
+        if (max_rank < 1) fail(ctx, ACI_E_ARG, "max_rank must be >= 1");
+        aci_opts o;
+        aci_opts_default(&o);
+        if (opts) o = *opts;
+        if (o.tol_kind != ACI_TOL_REL && o.tol_kind != ACI_TOL_ABS) fail(ctx, ACI_E_ARG, "bad tol_kind");
+        if (o.max_sweeps < 1) fail(ctx, ACI_E_ARG, "max_sweeps must be >= 1");
+        if (o.pivot_mode != ACI_PIVOT_FULL) fail(ctx, ACI_E_ARG, "unsupported pivot mode");
+        if (o.precision != ACI_PREC_FP64) fail(ctx, ACI_E_ARG, "unsupported precision");
+        if (o.out_memory != ACI_MEM_DEVICE && o.out_memory != ACI_MEM_HOST) fail(ctx, ACI_E_ARG, "bad out_memory");
+        validate_tt(ctx, a, "a");
+        const bool unary = op.kind == ACI_OP_ABS2_MUL;
+        if (!unary) {
+            if (!b) fail(ctx, ACI_E_ARG, "b must not be NULL for a binary op");
+            validate_tt(ctx, b, "b");
+            if (b->L != a->L) fail(ctx, ACI_E_SHAPE, "a and b differ in L");
+            for (int s = 0; s < a->L; ++s)
+                if (a->d[s] != b->d[s]) fail(ctx, ACI_E_SHAPE, "a and b differ in d");
+            if (b->dtype != a->dtype) fail(ctx, ACI_E_DTYPE, "a and b differ in dtype");
+            if (b->memory != a->memory) fail(ctx, ACI_E_ARG, "a and b differ in memory kind");
+        }
+        if (a->dtype == ACI_R64 && op.kind == ACI_OP_AFFINE)
+            for (int i = 0; i < 4; ++i)
+                if (op.c[i][1] != 0.0) fail(ctx, ACI_E_DTYPE, "complex coefficients on real inputs");
+        if (o.init) {
+            validate_tt(ctx, o.init, "init");
+            if (o.init->L != a->L || o.init->dtype != a->dtype) fail(ctx, ACI_E_SHAPE, "init differs from the inputs");
+            for (int s = 0; s < a->L; ++s)
+                if (o.init->d[s] != a->d[s]) fail(ctx, ACI_E_SHAPE, "init differs from the inputs in d");
+            for (int s = 1; s < a->L; ++s)
+                if (o.init->rank[s] > max_rank) fail(ctx, ACI_E_SHAPE, "init ranks exceed max_rank");
+        }
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        if (a->dtype == ACI_R64) return run_typed<double>(ctx, a, b, op, tol, max_rank, o, out, stats);
+        return run_typed<cplx>(ctx, a, b, op, tol, max_rank, o, out, stats);
+    } catch (Fail& f) {
+        return f.st;
+    } catch (...) {
+        ctx->err = "unexpected host exception";
+        return ACI_E_ARG;
+    }
+}
+
+aci_status aci_elementwise(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, double tol, int32_t max_rank,
+                           aci_tt* out) {
+    return aci_elementwise_ex(ctx, a, b, op, tol, max_rank, nullptr, out, nullptr);
+}
+
+aci_status aci_tt_release(aci_ctx* ctx, aci_tt* out) {
+    if (!ctx || !out) return ACI_E_ARG;
+    if (out->core) {
+        for (int s = 0; s < out->L; ++s) {
+            void* p = const_cast<void*>(out->core[s]);
+            if (!p) continue;
+            if (out->memory == ACI_MEM_HOST) std::free(p);
+            else dev_free(ctx, p);
+        }
+    }
+    std::free(const_cast<void**>(out->core));
+    std::free(const_cast<int32_t*>(out->d));
+    std::free(const_cast<int64_t*>(out->rank));
+    std::memset(out, 0, sizeof(*out));
+    return ACI_OK;
+}
+
+// ---------------------------------------------------------------- step-level entry points
+
+aci_status aci_k_frame_gemm(aci_ctx* ctx, int32_t dtype, const void* A, const int32_t* arows, int32_t M, int32_t K,
+                            int32_t lda, const void* B, const int32_t* bcols, int32_t N, int32_t ldb, void* C) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    try {
+        if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < 1) fail(ctx, ACI_E_ARG, "bad arguments");
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        int* dummy = reinterpret_cast<int*>(workspace(ctx, 256));
+        auto go = [&](auto tag) {
+            using T = decltype(tag);
+            aci::GemmArgs<T> g;
+            std::memset(&g, 0, sizeof(g));
+            g.A[0] = static_cast<const T*>(A);
+            g.B[0] = static_cast<const T*>(B);
+            g.C[0] = static_cast<T*>(C);
+            g.M[0] = dimc(M);
+            g.N[0] = dimc(N);
+            g.K[0] = dimc(K);
+            g.lda[0] = dimc(lda);
+            g.ldb[0] = dimc(ldb);
+            g.arow = arows;
+            g.bcol = bcols;
+            g.chi = dummy;
+            g.nprod = 1;
+            aci::launch_gemm<T>(g, M, N, ctx->stream);
+        };
+        if (dtype == ACI_R64) go(double());
+        else if (dtype == ACI_C128) go(cplx());
+        else fail(ctx, ACI_E_DTYPE, "unsupported dtype");
+        note_launch(ctx, "frame_gemm");
+        ck(ctx, cudaStreamSynchronize(ctx->stream), "frame_gemm");
+        return ACI_OK;
+    } catch (Fail& f) {
+        return f.st;
+    }
+}
+
+aci_status aci_k_pi_block(aci_ctx* ctx, int32_t dtype, int32_t nprod, const void* const* A, const void* const* B,
+                          int32_t M, int32_t N, const int32_t* K, aci_op op, void* Pi, double* maxabs) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    try {
+        if (!A || !B || !K || !Pi || M < 1 || N < 1 || nprod < 1 || nprod > 2) fail(ctx, ACI_E_ARG, "bad arguments");
+        if (op.kind < ACI_OP_MUL || op.kind > ACI_OP_AFFINE) fail(ctx, ACI_E_ARG, "unknown op kind");
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        char* ws = workspace(ctx, 512);
+        int* dummy = reinterpret_cast<int*>(ws);
+        unsigned long long* smax = reinterpret_cast<unsigned long long*>(ws + 256);
+        ck(ctx, cudaMemsetAsync(smax, 0, 8, ctx->stream), "memset");
+        auto go = [&](auto tag) {
+            using T = decltype(tag);
+            aci::GemmArgs<T> g;
+            std::memset(&g, 0, sizeof(g));
+            for (int n = 0; n < nprod; ++n) {
+                if (K[n] < 1) fail(ctx, ACI_E_ARG, "K must be >= 1");
+                g.A[n] = static_cast<const T*>(A[n]);
+                g.B[n] = static_cast<const T*>(B[n]);
+                g.K[n] = dimc(K[n]);
+                g.lda[n] = dimc(K[n]);
+                g.ldb[n] = dimc(N);
+            }
+            g.M[0] = dimc(M);
+            g.N[0] = dimc(N);
+            g.C[0] = static_cast<T*>(Pi);
+            g.chi = dummy;
+            g.nprod = nprod;
+            g.combine = 1;
+            g.op = make_op<T>(op);
+            g.smax = smax;
+            aci::launch_gemm<T>(g, M, N, ctx->stream);
+        };
+        if (dtype == ACI_R64) go(double());
+        else if (dtype == ACI_C128) go(cplx());
+        else fail(ctx, ACI_E_DTYPE, "unsupported dtype");
+        note_launch(ctx, "pi_block");
+        unsigned long long bits = 0;
+        ck(ctx, cudaMemcpyAsync(&bits, smax, 8, cudaMemcpyDeviceToHost, ctx->stream), "maxabs");
+        ck(ctx, cudaStreamSynchronize(ctx->stream), "pi_block");
+        if (maxabs) std::memcpy(maxabs, &bits, 8);
+        return ACI_OK;
+    } catch (Fail& f) {
+        return f.st;
+    }
+}
+
+aci_status aci_k_prrlu(aci_ctx* ctx, int32_t dtype, const void* Min, int32_t m, int32_t n, double tau, int32_t chimax,
+                       int32_t* piv_rows, int32_t* piv_cols, void* D, void* L, void* U, int32_t* k_out,
+                       double* eps_out) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    try {
+        if (!Min || !piv_rows || !piv_cols || !D || !k_out || !eps_out || m < 1 || n < 1 || chimax < 1 ||
+            !(tau >= 0.0))
+            fail(ctx, ACI_E_ARG, "bad arguments");
+        if ((long long)m * n >= (1LL << 31)) fail(ctx, ACI_E_SHAPE, "matrix too large");
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        const int kcap = std::min(std::min(m, n), chimax);
+        const int G = aci::prrlu_grid(n, ctx->num_sms);
+        auto go = [&](auto tag) {
+            using T = decltype(tag);
+            Carver c;
+            auto lay = [&](Carver& cv, int** kk, double** ee, int** er, int** chi_d, T** W, aci::PivRec** rec, T** slots) {
+                *kk = cv.take<int>(1);
+                *ee = cv.take<double>(1);
+                *er = cv.take<int>(1);
+                *chi_d = cv.take<int>(1);
+                *W = cv.take<T>((size_t)m * n);
+                *rec = cv.take<aci::PivRec>(2 * (size_t)G);
+                *slots = cv.take<T>(2 * (size_t)G * m);
+            };
+            int *kk, *er, *chi_d;
+            double* ee;
+            T* W;
+            aci::PivRec* rec;
+            T* slots;
+            lay(c, &kk, &ee, &er, &chi_d, &W, &rec, &slots);
+            Carver c2;
+            c2.base = workspace(ctx, c.off);
+            lay(c2, &kk, &ee, &er, &chi_d, &W, &rec, &slots);
+            ck(ctx, cudaMemsetAsync(er, 0, sizeof(int), ctx->stream), "memset");
+            aci::PrrluArgs<T> a;
+            std::memset(&a, 0, sizeof(a));
+            a.Min = static_cast<const T*>(Min);
+            a.m = dimc(m);
+            a.n = dimc(n);
+            a.chi = chi_d;
+            a.chimax = chimax;
+            a.out_chi_idx = -1;
+            a.k_out = kk;
+            a.eps_out = ee;
+            a.piv_rows = piv_rows;
+            a.piv_cols = piv_cols;
+            a.D = static_cast<T*>(D);
+            a.L = static_cast<T*>(L);
+            a.Lld = m;
+            a.U = static_cast<T*>(U);
+            a.Uld = n;
+            a.tol = tau;
+            a.rel = 0;
+            a.W = W;
+            a.rec = rec;
+            a.slots = slots;
+            a.mmax = m;
+            a.nmax = n;
+            a.epoch = ctx->epoch++;
+            a.err = er;
+            ck(ctx, aci::launch_prrlu<T>(a, G, ctx->stream), "prrlu launch");
+            note_launch(ctx, "prrlu");
+            int errflag = 0;
+            ck(ctx, cudaMemcpyAsync(k_out, kk, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "k");
+            ck(ctx, cudaMemcpyAsync(eps_out, ee, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "eps");
+            ck(ctx, cudaMemcpyAsync(&errflag, er, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "err");
+            ck(ctx, cudaStreamSynchronize(ctx->stream), "prrlu");
+            if (errflag & aci::DEVERR_TIMEOUT) fail(ctx, ACI_E_TIMEOUT, "pivot search wait timed out");
+            if (errflag & aci::DEVERR_NUMERIC) fail(ctx, ACI_E_NUMERIC, "non-finite pivot");
+            (void)kcap;
+        };
+        if (dtype == ACI_R64) go(double());
+        else if (dtype == ACI_C128) go(cplx());
+        else fail(ctx, ACI_E_DTYPE, "unsupported dtype");
+        return ACI_OK;
+    } catch (Fail& f) {
+        return f.st;
+    }
+}
+
+aci_status aci_k_tt_random(aci_ctx* ctx, int32_t dtype, uint64_t seed, int32_t L, const int32_t* d,
+                           const int64_t* rank, void* const* cores) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    try {
+        if (!d || !rank || !cores || L < 1) fail(ctx, ACI_E_ARG, "bad arguments");
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        std::vector<long long> off(L), cnt(L);
+        long long o = 0;
+        for (int s = 0; s < L; ++s) {
+            cnt[s] = rank[s] * d[s] * rank[s + 1];
+            off[s] = o;
+            o += cnt[s];
+        }
+        if (dtype == ACI_R64)
+            aci::launch_tt_random<double>(seed, L, off.data(), cnt.data(), reinterpret_cast<double* const*>(cores), ctx->stream);
+        else if (dtype == ACI_C128)
+            aci::launch_tt_random<cplx>(seed, L, off.data(), cnt.data(), reinterpret_cast<cplx* const*>(cores), ctx->stream);
+        else fail(ctx, ACI_E_DTYPE, "unsupported dtype");
+        note_launch(ctx, "tt_random");
+        ck(ctx, cudaStreamSynchronize(ctx->stream), "tt_random");
+        return ACI_OK;
+    } catch (Fail& f) {
+        return f.st;
+    }
+}
+
+aci_status aci_k_apply_pinv(aci_ctx* ctx, int32_t dtype, const void* Tm, int32_t R, int32_t k, const void* LI,
+                            const void* D, const void* UJ, void* Y) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    try {
+        if (!Tm || !LI || !D || !UJ || !Y || R < 1 || k < 1) fail(ctx, ACI_E_ARG, "bad arguments");
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        if (dtype == ACI_R64)
+            aci::launch_apply_pinv<double>(static_cast<const double*>(Tm), R, k, static_cast<const double*>(LI),
+                                           static_cast<const double*>(D), static_cast<const double*>(UJ),
+                                           static_cast<double*>(Y), ctx->stream);
+        else if (dtype == ACI_C128)
+            aci::launch_apply_pinv<cplx>(static_cast<const cplx*>(Tm), R, k, static_cast<const cplx*>(LI),
+                                         static_cast<const cplx*>(D), static_cast<const cplx*>(UJ),
+                                         static_cast<cplx*>(Y), ctx->stream);
+        else fail(ctx, ACI_E_DTYPE, "unsupported dtype");
+        note_launch(ctx, "apply_pinv");
+        ck(ctx, cudaStreamSynchronize(ctx->stream), "apply_pinv");
+        return ACI_OK;
+    } catch (Fail& f) {
+        return f.st;
+    }
+}
+
+}  // extern "C"

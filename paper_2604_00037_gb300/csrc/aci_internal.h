@@ -1,0 +1,111 @@
+// Internal interfaces between the ACI driver (aci_api.cu) and its kernels.
+#pragma once
+
+#include "aci_common.cuh"
+
+namespace aci {
+
+// C = gather_rows(A) * gather_cols(B) (batch: one output per product) or
+// C[0] = f(A^0 B^0, A^1 B^1) (combine). Row-major everything; ldc = N.
+template <class T> struct GemmArgs {
+    const T* A[2];
+    const T* B[2];
+    T* C[2];
+    DimE M[2], N[2];
+    DimE K[2], lda[2], ldb[2];
+    const int* arow;  // optional row gather of A (shared by the products)
+    const int* bcol;  // optional column gather of B
+    const int* chi;   // device rank array the DimE refer to
+    int nprod;
+    int combine;
+    OpParams<T> op;
+    unsigned long long* smax;  // optional running max |C| (bits of a non-negative double)
+    double* flops;             // optional: algorithmic flops of the launch are added here
+};
+
+template <class T> void launch_gemm(const GemmArgs<T>& g, int Mmax, int Nmax, cudaStream_t st);
+
+// One record per CTA per pivot step of the rank-revealing LU: the CTA's best candidate.
+struct __align__(16) PivRec {
+    unsigned long long tag;  // (epoch << 24) | (step + 1), written last with release semantics
+    double key;              // pivot key of the candidate (-1: the CTA has no active entry)
+    double vre, vim;         // candidate value
+    int r, c;                // candidate position (global row and column), -1 if none
+    int pad[2];
+};
+
+template <class T> struct PrrluArgs {
+    const T* Min;       // m x n row-major input, not modified
+    DimE m, n;          // live shape (device-resolved)
+    const int* chi;
+    int chimax;         // rank cap
+    int out_chi_idx;    // chi[out_chi_idx] = k on exit (-1: not written)
+    int* k_out;         // optional device int
+    double* eps_out;    // device double
+    double* flops;      // optional: algorithmic flops of the factorisation are added here
+    int* piv_rows;      // [kcap]
+    int* piv_cols;      // [kcap]
+    T* D;               // [kcap]
+    T* L;               // optional, column-major m x kcap, leading dimension Lld
+    int Lld;
+    T* U;               // optional, row-major kcap x n, leading dimension Uld
+    int Uld;
+    double tol;         // tau = tol * S (rel) or tol (abs)
+    int rel;
+    const unsigned long long* smax;  // S for rel
+    T* W;               // working copy, column-major, leading dimension mmax
+    PivRec* rec;        // [2][G]
+    T* slots;           // [2][G][mmax] candidate columns
+    int mmax, nmax;     // capacities
+    unsigned long long epoch;
+    int* err;           // device error flags (DevErr)
+};
+
+template <class T> cudaError_t launch_prrlu(const PrrluArgs<T>& a, int G, cudaStream_t st);
+template <class T> size_t prrlu_smem_bytes(int mmax, int nmax, int G);
+int prrlu_grid(int nmax, int num_sms);
+
+// Per-bond buffers used by the output assembly.
+template <class T> struct BondBuf {
+    const T* Pi;   // m_b x n_b row-major
+    const int* prow;
+    const int* pcol;
+    const T* D;
+    const T* Lm;   // column-major m_b x kcap, ld Lld
+    const T* Um;   // row-major kcap x n_b, ld Uld
+    int Lld, Uld;
+};
+
+// Y_s = T_s P_s^-1 for every site s (CI-canonical output), into Y[s] (row-major, contiguous).
+template <class T> struct AssembleArgs {
+    int L;
+    const int* chi;   // device ranks
+    const int* d;     // device local dimensions
+    const BondBuf<T>* bonds;  // [L-1] device array
+    T* const* Y;      // [L] device array of output pointers
+};
+template <class T> void launch_assemble(const AssembleArgs<T>& a, int Rmax, cudaStream_t st);
+
+// Y = T P^-1 with dense LI, D, UJ (k x k row-major): step-level entry point.
+template <class T> void launch_apply_pinv(const T* Tm, int R, int k, const T* LI, const T* D,
+                                          const T* UJ, T* Y, cudaStream_t st);
+
+// SplitMix64 counter-based random cores: entry e of the concatenation (site offsets off[s]).
+template <class T> void launch_tt_random(uint64_t seed, int L, const long long* off_host,
+                                         const long long* count_host, T* const* cores_host,
+                                         cudaStream_t st);
+
+// End-of-iteration bookkeeping on the device (one CTA): rank growth, fixed point, max eps.
+struct IterFlags {
+    int grew;
+    int fixed;
+    int err;
+    int pad;
+    double emax;
+    double S;
+};
+void launch_iter_check(int L, const int* chi, int* chi_prev, int* const* pcol, int* const* jprev,
+                       const double* eps_lr, const double* eps_rl, const unsigned long long* smax,
+                       const int* err, IterFlags* flags, int snapshot_only, cudaStream_t st);
+
+}  // namespace aci

@@ -1,0 +1,199 @@
+// Output assembly (CI-canonical form, Eq. (ycicanonical): Y_l = T_l P_l^-1), the random
+// initial guess of Algorithm 1, and the end-of-iteration test of Algorithm 1.
+#include "aci_internal.h"
+
+namespace aci {
+
+namespace {
+
+// ---------------------------------------------------------------- Y = T P^-1
+// P = LI D UJ (LI unit lower, UJ unit upper, in pivot order). For one row x of T:
+//   w UJ = x   (forward:  w_q = x_q - sum_{p<q} w_p UJ[p,q])
+//   z = w D^-1 (D_p = 0 is read as D_p^-1 = 0)
+//   y LI = z   (backward: y_p = z_p - sum_{q>p} y_q LI[q,p])
+// Each thread owns one row and keeps it in the output row (global, L1-resident).
+template <class T, class FT, class FLI, class FUJ, class FD>
+__device__ void solve_row(FT xval, int k, FLI li, FUJ uj, FD dv, T* y) {
+    for (int q = 0; q < k; ++q) {
+        T acc = xval(q);
+        for (int p = 0; p < q; ++p) acc = s_fms(y[p], uj(p, q), acc);
+        y[q] = acc;
+    }
+    for (int p = 0; p < k; ++p) {
+        const T dp = dv(p);
+        y[p] = s_iszero(dp) ? s_zero(T()) : s_div(y[p], dp);
+    }
+    for (int p = k - 1; p >= 0; --p) {
+        T acc = y[p];
+        for (int q = p + 1; q < k; ++q) acc = s_fms(y[q], li(q, p), acc);
+        y[p] = acc;
+    }
+}
+
+template <class T>
+__global__ void assemble_kernel(AssembleArgs<T> a) {
+    const int s = blockIdx.y;
+    const int L = a.L;
+    const int* chi = a.chi;
+    const int ds = a.d[s];
+    const int R = chi[s] * ds;                      // rows of Y_s: (alpha, sigma_s)
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int kout = chi[s + 1];                    // columns of Y_s
+    T* y = a.Y[s] + (size_t)r * kout;
+    // T_s row r: s = 0 -> Pi_0[sigma, J_1]; s >= 1 -> Pi_{s-1}[I_{s-1}[alpha], (sigma, :)].
+    const T* Pi;
+    size_t rowoff;
+    const int* colmap = nullptr;
+    int coloff = 0;
+    if (s == 0) {
+        const BondBuf<T>& b0 = a.bonds[0];
+        const int n0 = a.d[1] * chi[2];
+        Pi = b0.Pi;
+        rowoff = (size_t)r * n0;
+        colmap = b0.pcol;
+    } else {
+        const BondBuf<T>& bp = a.bonds[s - 1];
+        const int nprev = ds * chi[s + 1];
+        const int alpha = r / ds, sigma = r % ds;
+        Pi = bp.Pi;
+        rowoff = (size_t)bp.prow[alpha] * nprev;
+        coloff = sigma * kout;
+    }
+    auto xval = [&](int q) -> T { return Pi[rowoff + (colmap ? colmap[q] : coloff + q)]; };
+    if (s == L - 1) {  // Y_{L-1} = T_{L-1}
+        for (int q = 0; q < kout; ++q) y[q] = xval(q);
+        return;
+    }
+    const BondBuf<T>& bs = a.bonds[s];
+    auto li = [&](int q, int p) -> T { return bs.Lm[(size_t)p * bs.Lld + bs.prow[q]]; };
+    auto uj = [&](int p, int q) -> T { return bs.Um[(size_t)p * bs.Uld + bs.pcol[q]]; };
+    auto dv = [&](int p) -> T { return bs.D[p]; };
+    solve_row<T>(xval, kout, li, uj, dv, y);
+}
+
+template <class T>
+__global__ void apply_pinv_kernel(const T* Tm, int R, int k, const T* LI, const T* D, const T* UJ, T* Y) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    auto xval = [&](int q) -> T { return Tm[(size_t)r * k + q]; };
+    auto li = [&](int q, int p) -> T { return LI[(size_t)q * k + p]; };
+    auto uj = [&](int p, int q) -> T { return UJ[(size_t)p * k + q]; };
+    auto dv = [&](int p) -> T { return D[p]; };
+    solve_row<T>(xval, k, li, uj, dv, Y + (size_t)r * k);
+}
+
+// ---------------------------------------------------------------- SplitMix64 initial guess
+// Output c of the stream with seed s: mix(s + (c + 1) * 0x9E3779B97F4A7C15), mix being the
+// SplitMix64 finaliser (Steele, Lea, Flood, OOPSLA 2014). Uniform in [-1, 1): (z >> 11) 2^-52 - 1.
+__device__ __forceinline__ double sm64_uniform(unsigned long long seed, unsigned long long c) {
+    unsigned long long z = seed + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * 0x1p-52 - 1.0;
+}
+__device__ __forceinline__ void sm64_fill(double* p, unsigned long long seed, unsigned long long e) {
+    *p = sm64_uniform(seed, e);
+}
+__device__ __forceinline__ void sm64_fill(cplx* p, unsigned long long seed, unsigned long long e) {
+    *p = mkc(sm64_uniform(seed, 2 * e), sm64_uniform(seed, 2 * e + 1));
+}
+
+template <class T>
+__global__ void tt_random_kernel(unsigned long long seed, long long off, long long count, T* core) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+         e += (long long)gridDim.x * blockDim.x)
+        sm64_fill(core + e, seed, (unsigned long long)(off + e));
+}
+
+// ---------------------------------------------------------------- end-of-iteration test
+__global__ void iter_check_kernel(int L, const int* chi, int* chi_prev, int* const* pcol,
+                                  int* const* jprev, const double* eps_lr, const double* eps_rl,
+                                  const unsigned long long* smax, const int* err, IterFlags* flags,
+                                  int snapshot_only) {
+    __shared__ int s_grew, s_diff;
+    __shared__ double s_emax;
+    if (threadIdx.x == 0) { s_grew = 0; s_diff = 0; s_emax = 0.0; }
+    __syncthreads();
+    if (!snapshot_only) {
+        for (int s = 1 + threadIdx.x; s < L; s += blockDim.x)
+            if (chi[s] > chi_prev[s]) atomicOr(&s_grew, 1);
+        for (int b = threadIdx.x; b < L - 1; b += blockDim.x) {
+            const double e = fmax(eps_lr[b], eps_rl[b]);
+            // non-negative doubles order like their bit patterns
+            atomicMax(reinterpret_cast<unsigned long long*>(&s_emax), (unsigned long long)__double_as_longlong(e));
+        }
+        // fixed point: every J set (positions, in order) equal to the previous iteration's
+        for (int b = 0; b < L - 1; ++b) {
+            const int k = chi[b + 1];
+            if (k != chi_prev[b + 1]) { if (threadIdx.x == 0) s_diff = 1; continue; }
+            for (int q = threadIdx.x; q < k; q += blockDim.x)
+                if (pcol[b][q] != jprev[b][q]) s_diff = 1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !snapshot_only) {
+        flags->grew = s_grew;
+        flags->fixed = s_diff ? 0 : 1;
+        flags->emax = s_emax;
+        flags->S = __longlong_as_double((long long)*smax);
+        flags->err = *err;
+    }
+    __syncthreads();
+    // snapshot ranks and J sets for the next iteration's comparison
+    for (int s = threadIdx.x; s <= L; s += blockDim.x) chi_prev[s] = chi[s];
+    for (int b = 0; b < L - 1; ++b) {
+        const int k = chi[b + 1];
+        for (int q = threadIdx.x; q < k; q += blockDim.x) jprev[b][q] = pcol[b][q];
+    }
+}
+
+}  // namespace
+
+template <class T>
+void launch_assemble(const AssembleArgs<T>& a, int Rmax, cudaStream_t st) {
+    const int nt = 64;
+    dim3 grid((Rmax + nt - 1) / nt, a.L);
+    assemble_kernel<T><<<grid, nt, 0, st>>>(a);
+}
+
+template <class T>
+void launch_apply_pinv(const T* Tm, int R, int k, const T* LI, const T* D, const T* UJ, T* Y,
+                       cudaStream_t st) {
+    if (R <= 0) return;
+    const int nt = 64;
+    apply_pinv_kernel<T><<<(R + nt - 1) / nt, nt, 0, st>>>(Tm, R, k, LI, D, UJ, Y);
+}
+
+template <class T>
+void launch_tt_random(uint64_t seed, int L, const long long* off, const long long* count,
+                      T* const* cores, cudaStream_t st) {
+    for (int s = 0; s < L; ++s) {
+        if (count[s] <= 0) continue;
+        const int nt = 256;
+        long long nb = (count[s] + nt - 1) / nt;
+        if (nb > 4096) nb = 4096;
+        tt_random_kernel<T><<<(int)nb, nt, 0, st>>>(seed, off[s], count[s], cores[s]);
+    }
+}
+
+void launch_iter_check(int L, const int* chi, int* chi_prev, int* const* pcol, int* const* jprev,
+                       const double* eps_lr, const double* eps_rl, const unsigned long long* smax,
+                       const int* err, IterFlags* flags, int snapshot_only, cudaStream_t st) {
+    iter_check_kernel<<<1, 256, 0, st>>>(L, chi, chi_prev, pcol, jprev, eps_lr, eps_rl, smax, err,
+                                         flags, snapshot_only);
+}
+
+template void launch_assemble<double>(const AssembleArgs<double>&, int, cudaStream_t);
+template void launch_assemble<cplx>(const AssembleArgs<cplx>&, int, cudaStream_t);
+template void launch_apply_pinv<double>(const double*, int, int, const double*, const double*,
+                                        const double*, double*, cudaStream_t);
+template void launch_apply_pinv<cplx>(const cplx*, int, int, const cplx*, const cplx*, const cplx*,
+                                      cplx*, cudaStream_t);
+template void launch_tt_random<double>(uint64_t, int, const long long*, const long long*,
+                                       double* const*, cudaStream_t);
+template void launch_tt_random<cplx>(uint64_t, int, const long long*, const long long*,
+                                     cplx* const*, cudaStream_t);
+
+}  // namespace aci
