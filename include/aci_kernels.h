@@ -68,6 +68,25 @@ aci_status aci_k_tt_random(aci_ctx *ctx, int32_t dtype, uint64_t seed, int32_t L
 aci_status aci_k_apply_pinv(aci_ctx *ctx, int32_t dtype, const void *T, int32_t R, int32_t k,
                             const void *LI, const void *D, const void *UJ, void *Y);
 
+/* The pivot search of aci_k_prrlu for callers that cannot allocate device memory; the paper
+ * has no counterpart (it concerns how this library obtains scratch memory, not the method).
+ * Such callers include code inside a host application that owns all device memory and forbids
+ * libraries from allocating behind its back, code with a fixed memory budget, and code that
+ * must not enter a device allocator (which can block on the device or take locks).
+ * The call allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine. Its
+ * scratch is one 8 MiB file-scope device array that every GPU loading the library holds until
+ * the process exits. Arguments and results are those of aci_k_prrlu, except:
+ *  cuda_stream  the cudaStream_t to run on (NULL = legacy default stream), on the current device;
+ *  limits       m <= 4096, n <= 4096, m * n <= 262144, else ACI_E_SHAPE and nothing runs.
+ * No aci_ctx is involved, so there is no aci_last_error() message: the status says what failed.
+ * The first call on each device (with that device current) looks up the array's address; make
+ * that first call before any stream capture. All calls on a device share the array: calls that
+ * overlap on the GPU race and must be serialised by the caller. The call returns after the
+ * stream has synchronised. */
+aci_status aci_k_prrlu_static(void *cuda_stream, int32_t dtype, const void *Min, int32_t m, int32_t n,
+                              double tau, int32_t chimax, int32_t *piv_rows, int32_t *piv_cols,
+                              void *D, void *L, void *U, int32_t *k_out, double *eps_out);
+
 #ifdef __cplusplus
 }
 #endif
