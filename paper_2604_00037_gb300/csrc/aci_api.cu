@@ -209,8 +209,9 @@ struct Run {
     aci::IterFlags* flags = nullptr;
     T* ones = nullptr;
     T* W = nullptr;
-    aci::PivRec* rec = nullptr;
-    T* slots = nullptr;
+    unsigned long long* ll = nullptr;  // pivot-search exchange words
+    size_t ll_words = 0;
+    unsigned int prrlu_launches = 0;   // launches since the exchange area was last cleared
     int Gmax = 1;
     size_t wcap = 0;
     int mmax_all = 1;
@@ -219,7 +220,20 @@ struct Run {
     int** pcol_dev = nullptr;
     int** jprev_dev = nullptr;
 
+    static constexpr bool is_cplx = sizeof(T) == sizeof(cplx);
+
     const T* Xp(int n, int s) const { return Xv[n][s]; }
+
+    // Tag base of the next pivot-search launch; clears the exchange area when the tags of
+    // this area are used up (launches since the last clear < 2^19).
+    unsigned int next_tagbase() {
+        if (prrlu_launches >= aci::kPrrluMaxLaunches) {
+            ck(ctx, cudaMemsetAsync(ll, 0, ll_words * sizeof(unsigned long long), st), "clear exchange");
+            prrlu_launches = 0;
+        }
+        ++prrlu_launches;
+        return prrlu_launches << aci::kPrrluStepBits;
+    }
 
     void layout(Carver& c) {
         for (int n = 0; n < N; ++n) {
@@ -272,8 +286,7 @@ struct Run {
         flags = c.take<aci::IterFlags>(1);
         ones = c.take<T>(1);
         W = c.take<T>(wcap);
-        rec = c.take<aci::PivRec>(2 * (size_t)Gmax);
-        slots = c.take<T>(2 * (size_t)Gmax * mmax_all);
+        ll = c.take<unsigned long long>(ll_words);
         bonds_dev = c.take<aci::BondBuf<T>>(std::max(nb, 1));
         Yptr_dev = c.take<T*>(L);
         pcol_dev = c.take<int*>(std::max(nb, 1));
@@ -313,7 +326,9 @@ struct Run {
             kcap[b] = cap[b + 1];
             wcap = std::max(wcap, (size_t)mcap[b] * ncap[b]);
             mmax_all = std::max(mmax_all, mcap[b]);
-            Gmax = std::max(Gmax, aci::prrlu_grid(ncap[b], ctx->num_sms));
+            const int G = aci::prrlu_grid(mcap[b], ncap[b], ctx->num_sms);
+            Gmax = std::max(Gmax, G);
+            ll_words = std::max(ll_words, aci::prrlu_ll_words(mcap[b], G, is_cplx));
             if ((long long)mcap[b] * ncap[b] >= (1LL << 31))
                 fail(ctx, ACI_E_SHAPE, "a Pi block would exceed 2^31 entries");
         }
@@ -321,7 +336,9 @@ struct Run {
             const int m = ry[s], n = d[s] * cap[s + 1];
             wcap = std::max(wcap, (size_t)m * n);
             mmax_all = std::max(mmax_all, m);
-            Gmax = std::max(Gmax, aci::prrlu_grid(n, ctx->num_sms));
+            const int G = aci::prrlu_grid(m, n, ctx->num_sms);
+            Gmax = std::max(Gmax, G);
+            ll_words = std::max(ll_words, aci::prrlu_ll_words(m, G, is_cplx));
         }
     }
 
@@ -365,14 +382,13 @@ struct Run {
         a.rel = rel;
         a.smax = S;
         a.W = W;
-        a.rec = rec;
-        a.slots = slots;
+        a.ll = ll;
+        a.tagbase = next_tagbase();
         a.mmax = mm;
         a.nmax = nn;
-        a.epoch = ctx->epoch++;
         a.err = err;
         a.flops = flops_of(ACI_KCLASS_PIVOT);
-        const int G = aci::prrlu_grid(nn, ctx->num_sms);
+        const int G = aci::prrlu_grid(mm, nn, ctx->num_sms);
         cudaEvent_t e = pre(ACI_KCLASS_PIVOT);
         ck(ctx, aci::launch_prrlu<T>(a, G, st), "prrlu launch");
         post(ACI_KCLASS_PIVOT, e, "prrlu");
@@ -474,6 +490,8 @@ struct Run {
         ck(ctx, cudaMemsetAsync(err, 0, sizeof(int), st), "memset");
         ck(ctx, cudaMemsetAsync(smax, 0, sizeof(unsigned long long), st), "memset");
         ck(ctx, cudaMemsetAsync(kflops, 0, 4 * sizeof(double), st), "memset");
+        ck(ctx, cudaMemsetAsync(ll, 0, ll_words * sizeof(unsigned long long), st), "clear exchange");
+        prrlu_launches = 0;
         T one_h;
         std::memset(&one_h, 0, sizeof(T));
         *reinterpret_cast<double*>(&one_h) = 1.0;
@@ -818,7 +836,7 @@ aci_status aci_elementwise_ex(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, ac
         if (!a || !out) fail(ctx, ACI_E_ARG, "a and out must not be NULL");
         if (op.kind < ACI_OP_MUL || op.kind > ACI_OP_AFFINE) fail(ctx, ACI_E_ARG, "unknown op kind");
         if (!(tol >= 0.0) || !(tol < INFINITY)) fail(ctx, ACI_E_ARG, "tol must be finite and >= 0");
-        if (max_rank < 1) fail(ctx, ACI_E_ARG, "max_rank must be >= 1");
+        if (max_rank < 1 || max_rank > 8190) fail(ctx, ACI_E_ARG, "max_rank must be in [1, 8190]");
         aci_opts o;
         aci_opts_default(&o);
         if (opts) o = *opts;
@@ -981,29 +999,30 @@ aci_status aci_k_prrlu(aci_ctx* ctx, int32_t dtype, const void* Min, int32_t m, 
         if ((long long)m * n >= (1LL << 31)) fail(ctx, ACI_E_SHAPE, "matrix too large");
         ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
         const int kcap = std::min(std::min(m, n), chimax);
-        const int G = aci::prrlu_grid(n, ctx->num_sms);
+        if (kcap > 8190) fail(ctx, ACI_E_SHAPE, "more than 8190 pivots requested");
+        const int G = aci::prrlu_grid(m, n, ctx->num_sms);
         auto go = [&](auto tag) {
             using T = decltype(tag);
+            const size_t nll = aci::prrlu_ll_words(m, G, sizeof(T) == sizeof(cplx));
             Carver c;
-            auto lay = [&](Carver& cv, int** kk, double** ee, int** er, int** chi_d, T** W, aci::PivRec** rec, T** slots) {
+            auto lay = [&](Carver& cv, int** kk, double** ee, int** er, int** chi_d, T** W, unsigned long long** ll) {
                 *kk = cv.take<int>(1);
                 *ee = cv.take<double>(1);
                 *er = cv.take<int>(1);
                 *chi_d = cv.take<int>(1);
                 *W = cv.take<T>((size_t)m * n);
-                *rec = cv.take<aci::PivRec>(2 * (size_t)G);
-                *slots = cv.take<T>(2 * (size_t)G * m);
+                *ll = cv.take<unsigned long long>(nll);
             };
             int *kk, *er, *chi_d;
             double* ee;
             T* W;
-            aci::PivRec* rec;
-            T* slots;
-            lay(c, &kk, &ee, &er, &chi_d, &W, &rec, &slots);
+            unsigned long long* ll;
+            lay(c, &kk, &ee, &er, &chi_d, &W, &ll);
             Carver c2;
             c2.base = workspace(ctx, c.off);
-            lay(c2, &kk, &ee, &er, &chi_d, &W, &rec, &slots);
+            lay(c2, &kk, &ee, &er, &chi_d, &W, &ll);
             ck(ctx, cudaMemsetAsync(er, 0, sizeof(int), ctx->stream), "memset");
+            ck(ctx, cudaMemsetAsync(ll, 0, nll * sizeof(unsigned long long), ctx->stream), "clear exchange");
             aci::PrrluArgs<T> a;
             std::memset(&a, 0, sizeof(a));
             a.Min = static_cast<const T*>(Min);
@@ -1024,11 +1043,10 @@ aci_status aci_k_prrlu(aci_ctx* ctx, int32_t dtype, const void* Min, int32_t m, 
             a.tol = tau;
             a.rel = 0;
             a.W = W;
-            a.rec = rec;
-            a.slots = slots;
+            a.ll = ll;
+            a.tagbase = 1u << aci::kPrrluStepBits;
             a.mmax = m;
             a.nmax = n;
-            a.epoch = ctx->epoch++;
             a.err = er;
             ck(ctx, aci::launch_prrlu<T>(a, G, ctx->stream), "prrlu launch");
             note_launch(ctx, "prrlu");

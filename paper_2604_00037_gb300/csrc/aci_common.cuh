@@ -75,6 +75,20 @@ __device__ __forceinline__ double s_mag(cplx a) { return __dsqrt_rn(s_key(a)); }
 __device__ __forceinline__ double key_to_mag(double k, double) { return k; }
 __device__ __forceinline__ double key_to_mag(double k, cplx) { return __dsqrt_rn(k); }
 
+// Bits of the pivot key of a value. Keys are non-negative doubles, which order like their bit
+// patterns, so maxima are taken on 64-bit integers (the FP64 pipe is scarce on GB300). For real
+// values the key |v| is formed by clearing the sign bit: bit-identical to fabs, no FP64 op.
+__device__ __forceinline__ unsigned long long key_of(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    // an explicit integer AND: left to itself the compiler turns the mask back into fabs,
+    // which on this GPU costs an FP64 operation per entry
+    asm("and.b64 %0, %0, 0x7FFFFFFFFFFFFFFF;" : "+l"(b));
+    return b;
+}
+__device__ __forceinline__ unsigned long long key_of(cplx v) {
+    return (unsigned long long)__double_as_longlong(s_key(v));
+}
+
 // |a|^2 a (the oracle computes (a*a)*a for real and (re*re + im*im) * a for complex).
 __device__ __forceinline__ double abs2_mul(double a) { return (a * a) * a; }
 __device__ __forceinline__ cplx abs2_mul(cplx a) {

@@ -99,8 +99,9 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
         atomicAdd(g.flops, f);
     }
 
-    // Epilogue: f over the products (combine) or a plain store (batch); running max |C|.
-    double mx = 0.0;
+    // Epilogue: f over the products (combine) or a plain store (batch); running max |C|,
+    // taken on key bits (integer max) and turned into a magnitude once per warp.
+    unsigned long long mk = 0;
     T* C = g.C[z];
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
@@ -111,19 +112,22 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
             if (gr < M && gc < N) {
                 T v = g.combine ? apply_f(g.op, acc[0][i][j], acc[1][i][j]) : acc[0][i][j];
                 C[(size_t)gr * N + gc] = v;
-                const double mg = s_mag(v);
-                mx = (mg > mx || mg != mg) ? mg : mx;  // NaN propagates into the maximum
+                const unsigned long long k = key_of(v);
+                mk = k > mk ? k : mk;  // NaN bits sort above +inf
             }
         }
     }
     if (g.smax) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            const double o = __shfl_xor_sync(0xffffffffu, mx, off);
-            mx = (o > mx || o != o) ? o : mx;
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, mk, off);
+            mk = o > mk ? o : mk;
         }
-        // Non-negative doubles order like their bit patterns; NaN bits sort above +inf.
-        if ((tid & 31) == 0) atomicMax(g.smax, (unsigned long long)__double_as_longlong(mx));
+        // |v| = key for real, sqrt(key) for complex; sqrt is monotone, so the max commutes with it.
+        if ((tid & 31) == 0) {
+            const double mag = key_to_mag(__longlong_as_double((long long)mk), T());
+            atomicMax(g.smax, (unsigned long long)__double_as_longlong(mag));
+        }
     }
 }
 

@@ -25,15 +25,6 @@ template <class T> struct GemmArgs {
 
 template <class T> void launch_gemm(const GemmArgs<T>& g, int Mmax, int Nmax, cudaStream_t st);
 
-// One record per CTA per pivot step of the rank-revealing LU: the CTA's best candidate.
-struct __align__(16) PivRec {
-    unsigned long long tag;  // (epoch << 24) | (step + 1), written last with release semantics
-    double key;              // pivot key of the candidate (-1: the CTA has no active entry)
-    double vre, vim;         // candidate value
-    int r, c;                // candidate position (global row and column), -1 if none
-    int pad[2];
-};
-
 template <class T> struct PrrluArgs {
     const T* Min;       // m x n row-major input, not modified
     DimE m, n;          // live shape (device-resolved)
@@ -53,17 +44,24 @@ template <class T> struct PrrluArgs {
     double tol;         // tau = tol * S (rel) or tol (abs)
     int rel;
     const unsigned long long* smax;  // S for rel
-    T* W;               // working copy, column-major, leading dimension mmax
-    PivRec* rec;        // [2][G]
-    T* slots;           // [2][G][mmax] candidate columns
-    int mmax, nmax;     // capacities
-    unsigned long long epoch;
+    T* W;               // global working copy (column-major, ld mmax) when the block does not fit in shared memory
+    unsigned long long* ll;  // exchange words: prrlu_ll_words(mmax, G, complex) of them
+    unsigned int tagbase;    // tags are tagbase + step + 1; distinct per launch since the area was cleared
+    int mmax, nmax;     // capacities of this launch
     int* err;           // device error flags (DevErr)
+    // filled by launch_prrlu
+    int epc, wcap_elems, wcap_cols;
 };
 
+// Target entries of the pivot block per CTA: small blocks run in one CTA (no grid sync).
+constexpr int kPrrluEpc = 2048;
+// Steps per launch are < 2^13; tag bases are (launch number within a cleared area) << 13.
+constexpr int kPrrluStepBits = 13;
+constexpr unsigned int kPrrluMaxLaunches = (1u << (32 - kPrrluStepBits)) - 1;
+
 template <class T> cudaError_t launch_prrlu(const PrrluArgs<T>& a, int G, cudaStream_t st);
-template <class T> size_t prrlu_smem_bytes(int mmax, int nmax, int G);
-int prrlu_grid(int nmax, int num_sms);
+int prrlu_grid(int mmax, int nmax, int num_sms);
+size_t prrlu_ll_words(int mmax, int G, bool cplx_values);
 
 // Per-bond buffers used by the output assembly.
 template <class T> struct BondBuf {

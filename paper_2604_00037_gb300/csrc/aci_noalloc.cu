@@ -13,10 +13,10 @@
 //  * The array is kStaticBytes (8 MiB). Every GPU that loads the library holds it until the
 //    process exits. Inputs must satisfy m <= 4096, n <= 4096 and m * n <= 262144; larger
 //    shapes are rejected with ACI_E_SHAPE before anything runs.
-//  * Every call on a device uses the same array and leaves its contents behind; the call zeroes
-//    what must start at zero (the error flag) and tags its records with a per-call number, so
-//    stale contents are never read. Calls that overlap on the GPU (two streams, or two host
-//    threads at once) race on the array: serialise them.
+//  * Every call on a device uses the same array and leaves its contents behind; each call first
+//    zeroes what must start at zero (the error flag and the words the CTAs exchange at every
+//    pivot step), so stale contents are never read. Calls that overlap on the GPU (two streams,
+//    or two host threads at once) race on the array: serialise them.
 //  * The first call on each device, with that device current, looks up the array's device
 //    address (cudaGetSymbolAddress) and caches it. Make that first call before any stream
 //    capture.
@@ -69,7 +69,7 @@ aci_status static_scratch(int dev, unsigned char** base, int* num_sms, unsigned 
     }
     *base = s.base;
     *num_sms = s.num_sms;
-    *call_id = ++s.calls;  // records of this call are tagged (call_id << 24) | (step + 1)
+    *call_id = ++s.calls;  // calls made on this device so far
     return ACI_OK;
 }
 
@@ -97,18 +97,20 @@ aci_status run_static(cudaStream_t st, const void* Min, int m, int n, double tau
     unsigned long long call_id = 0;
     aci_status s = static_scratch(dev, &base, &sms, &call_id);
     if (s != ACI_OK) return s;
-    const int G = aci::prrlu_grid(n, sms);
+    const int G = aci::prrlu_grid(m, n, sms);
     Bump b{base};
     int* k_dev = b.take<int>(1);
     double* eps_dev = b.take<double>(1);
     int* err_dev = b.take<int>(1);
     int* chi_dev = b.take<int>(1);
-    aci::PivRec* rec = b.take<aci::PivRec>(2 * size_t(G));
+    const size_t nll = aci::prrlu_ll_words(m, G, sizeof(T) == sizeof(aci::cplx));
+    unsigned long long* ll = b.take<unsigned long long>(nll);
     T* W = b.take<T>(size_t(m) * n);
-    T* slots = b.take<T>(2 * size_t(G) * m);
     if (b.off > kStaticBytes) return ACI_E_SHAPE;  // unreachable within the documented limits
 
-    if (cudaMemsetAsync(err_dev, 0, sizeof(int), st) != cudaSuccess) {
+    // zero what must start at zero: the error flag and the pivot-search exchange words
+    if (cudaMemsetAsync(err_dev, 0, sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(ll, 0, nll * sizeof(unsigned long long), st) != cudaSuccess) {
         cudaGetLastError();
         return ACI_E_CUDA;
     }
@@ -132,11 +134,10 @@ aci_status run_static(cudaStream_t st, const void* Min, int m, int n, double tau
     a.tol = tau;
     a.rel = 0;
     a.W = W;
-    a.rec = rec;
-    a.slots = slots;
+    a.ll = ll;
+    a.tagbase = 1u << aci::kPrrluStepBits;
     a.mmax = m;
     a.nmax = n;
-    a.epoch = call_id;
     a.err = err_dev;
     if (aci::launch_prrlu<T>(a, G, st) != cudaSuccess) {
         cudaGetLastError();

@@ -5,18 +5,28 @@
 // (p >= 1 and |pivot| <= tau), and otherwise eliminates it with a Schur-complement update
 // S <- S - (S[:, j] / S[i, j]) S[i, :] on the unused rows and columns. Instead of the
 // paper's in-place row and column swaps, used rows and columns are masked: the pivots,
-// D, L and U are the same (L and U are stored in original row / column order).
+// D, L and U are the same (L and U are stored in original row / column order). The
+// multipliers use one reciprocal of the pivot per step.
 //
-// GB300 design: one cooperative launch per factorisation. CTA g owns a contiguous block of
-// columns, kept column-major in a scratch copy W (L2-resident). Every step has exactly one
-// grid-wide synchronisation, carried by the data itself: each CTA publishes its best
-// candidate (value and position) and that candidate's whole column in a record tagged with
-// the step number (release store); every CTA then waits for the G tags of the step (acquire
-// loads, bounded spin), picks the same winner, and reads the winner's column for its own
-// update. Records and columns are double-buffered by step parity, so no CTA can overwrite
-// a record another CTA has not read yet (it would first need that CTA's next record).
+// GB300 design. One cooperative launch per factorisation; the number of CTAs that take part
+// is chosen on the device from the live shape (about kEpc entries per CTA, at least one column
+// each), so small blocks run in one CTA with no grid-wide synchronisation at all. CTA g owns a
+// contiguous block of columns, kept column-major in shared memory when the worst case fits
+// (else in an L2-resident global copy). The pivot steps are strictly sequential; each one
+// costs exactly one exchange between CTAs, made of self-validating 8-byte words: the low 32
+// bits carry data, the high 32 bits the step's tag. Every CTA writes its best candidate
+// (key, position, value) and that candidate's column as such words, then polls the G records
+// of the step; because every 8-byte word is written and read atomically and carries its own
+// tag, no fence, acquire or release is needed, and a word from an older step can never be
+// mistaken for a current one. Records and columns alternate between two buffers by step
+// parity: a CTA can only overwrite a buffer after every other CTA has published its next
+// record, which each does only after it has read the buffer. The caller clears the exchange
+// area once per sequence of launches and gives each launch a distinct tag base.
 // The Schur update of step p is fused with the local argmax of step p+1.
 #include <climits>
+#include <cstdlib>
+
+#include <cooperative_groups.h>
 
 #include "aci_internal.h"
 
@@ -27,31 +37,115 @@ namespace {
 constexpr int PT = 256;
 constexpr int NWARP = PT / 32;
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+template <class T> struct Words;  // 8-byte exchange words per value
+template <> struct Words<double> { static constexpr int value = 2; };
+template <> struct Words<cplx> { static constexpr int value = 4; };
+constexpr int kRecWords = 8;      // key (2), position (1), value (up to 4), spare (1)
+
+__device__ __forceinline__ void st_word(unsigned long long* p, unsigned int data, unsigned int tag) {
+    const unsigned long long v = ((unsigned long long)tag << 32) | data;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_word(const unsigned long long* p) {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-// Loads of data written by other CTAs during this launch go through L2 (never a stale L1 line).
-__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
-__device__ __forceinline__ cplx ldcg(const cplx* p) {
+__device__ __forceinline__ unsigned int word_tag(unsigned long long w) { return (unsigned int)(w >> 32); }
+__device__ __forceinline__ double ldcg_val(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ cplx ldcg_val(const cplx* p) {
     const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
     return mkc(v.x, v.y);
 }
-__device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned int word_data(unsigned long long w) { return (unsigned int)w; }
 
-__device__ __forceinline__ bool better(double k1, int l1, double k2, int l2) {
+__device__ __forceinline__ void put_double(unsigned long long* p, double v, unsigned int tag) {
+    st_word(p, (unsigned int)__double2hiint(v), tag);
+    st_word(p + 1, (unsigned int)__double2loint(v), tag);
+}
+__device__ __forceinline__ void put_val(unsigned long long* p, double v, unsigned int tag) { put_double(p, v, tag); }
+__device__ __forceinline__ void put_val(unsigned long long* p, cplx v, unsigned int tag) {
+    put_double(p, v.re, tag);
+    put_double(p + 2, v.im, tag);
+}
+__device__ __forceinline__ double dbl_of(unsigned long long hi, unsigned long long lo) {
+    return __hiloint2double((int)word_data(hi), (int)word_data(lo));
+}
+__device__ __forceinline__ void val_of(const unsigned long long* w, double& v) { v = dbl_of(w[0], w[1]); }
+__device__ __forceinline__ void val_of(const unsigned long long* w, cplx& v) {
+    v = mkc(dbl_of(w[0], w[1]), dbl_of(w[2], w[3]));
+}
+
+// Read NW consecutive words once all of them carry `tag`; false after the spin limit.
+template <int NW>
+__device__ __forceinline__ bool get_words(const unsigned long long* p, unsigned int tag, unsigned long long* out) {
+    long long spins = 0;
+    for (;;) {
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+            out[i] = ld_word(p + i);
+            ok &= word_tag(out[i]) == tag;
+        }
+        if (ok) return true;
+        if (++spins > kSpinLimit) return false;
+    }
+}
+
+// Keys are non-negative doubles (|v|, or re^2 + im^2), so they order like their bit patterns:
+// the argmax compares 64-bit integers (the FP64 pipe, 2 ops/clk/SM on GB300, is left to the
+// Schur update). A NaN key sorts above +inf and surfaces as a numeric error at the stop test.
+// (key bits, linear index) = (0, INT_MAX) means "no candidate"; any real entry beats it.
+typedef unsigned long long kbits_t;
+__device__ __forceinline__ kbits_t key_bits(double k) { return (kbits_t)__double_as_longlong(k); }
+
+// Round a shared-memory pointer up to 16 bytes (matches the padding in the byte counts).
+template <class P>
+__device__ __forceinline__ P* align16(void* p) {
+    return reinterpret_cast<P*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
+}
+
+// The step's decision, taken by one thread and read by all (keeps FP64 work off the others).
+template <class T> struct __align__(16) Decision {
+    int code;  // 0 = accept the pivot, 1 = stop, 2 = stop on a non-finite pivot
+    int zpiv;  // the pivot is exactly zero (all-zero block)
+    double eps;
+    T inv;     // 1 / pivot (0 when zpiv)
+};
+template <class T>
+__device__ __forceinline__ void decide(Decision<T>* d, kbits_t wkey, int wlin, T piv, int p, int kmax, double tau) {
+    int code = 0;
+    double e = 0.0;
+    d->zpiv = 0;
+    d->inv = s_zero(T());
+    if (wlin == INT_MAX) {
+        code = 1;
+    } else {
+        const double mag = key_to_mag(__longlong_as_double((long long)wkey), T());
+        if (wkey >= key_bits(INFINITY)) {
+            code = 2;
+            e = mag;
+        } else if (p == kmax || (p >= 1 && mag <= tau)) {
+            code = 1;
+            e = mag;
+        } else if (s_iszero(piv)) {
+            d->zpiv = 1;
+        } else {
+            d->inv = s_div(s_one(T()), piv);
+        }
+    }
+    d->code = code;
+    d->eps = e;
+}
+__device__ __forceinline__ bool better(kbits_t k1, int l1, kbits_t k2, int l2) {
     return k1 > k2 || (k1 == k2 && l1 < l2);
 }
 
 // Block-wide (key, linear index) argmax; the result is returned to every thread.
-__device__ __forceinline__ void block_argmax(double& key, int& lin, double* skey, int* slin) {
+__device__ __forceinline__ void block_argmax(kbits_t& key, int& lin, kbits_t* skey, int* slin) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        const double ok = __shfl_xor_sync(0xffffffffu, key, off);
+        const kbits_t ok = __shfl_xor_sync(0xffffffffu, key, off);
         const int ol = __shfl_xor_sync(0xffffffffu, lin, off);
         if (better(ok, ol, key, lin)) { key = ok; lin = ol; }
     }
@@ -60,11 +154,11 @@ __device__ __forceinline__ void block_argmax(double& key, int& lin, double* skey
     if (lane == 0) { skey[warp] = key; slin[warp] = lin; }
     __syncthreads();
     if (warp == 0) {
-        key = lane < NWARP ? skey[lane] : -2.0;
+        key = lane < NWARP ? skey[lane] : 0ull;
         lin = lane < NWARP ? slin[lane] : INT_MAX;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            const double ok = __shfl_xor_sync(0xffffffffu, key, off);
+            const kbits_t ok = __shfl_xor_sync(0xffffffffu, key, off);
             const int ol = __shfl_xor_sync(0xffffffffu, lin, off);
             if (better(ok, ol, key, lin)) { key = ok; lin = ol; }
         }
@@ -75,38 +169,64 @@ __device__ __forceinline__ void block_argmax(double& key, int& lin, double* skey
     lin = slin[NWARP];
 }
 
-__device__ __forceinline__ void set_val(PivRec* r, double v) { r->vre = v; r->vim = 0.0; }
-__device__ __forceinline__ void set_val(PivRec* r, cplx v) { r->vre = v.re; r->vim = v.im; }
-__device__ __forceinline__ void get_val(const PivRec* r, double& v) { v = __ldcg(&r->vre); }
-__device__ __forceinline__ void get_val(const PivRec* r, cplx& v) { v = mkc(__ldcg(&r->vre), __ldcg(&r->vim)); }
+__host__ __device__ inline int live_ctas(long long mn, int n, int G, int epc) {
+    long long g = (mn + epc - 1) / epc;
+    if (g < 1) g = 1;
+    if (g > G) g = G;
+    if (g > n) g = n;
+    return (int)g;
+}
 
-__device__ __forceinline__ double sanitize_key(double k) { return (k != k) ? INFINITY : k; }
-
-template <class T>
+template <class T, bool SMEMW>
 __global__ void __launch_bounds__(PT) prrlu_kernel(PrrluArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int WPV = Words<T>::value;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
     const int m = dimv(a.m, a.chi), n = dimv(a.n, a.chi);
-    const int c0 = (int)(((long long)n * g) / G), c1 = (int)(((long long)n * (g + 1)) / G);
+    const int Ge = live_ctas((long long)m * n, n, G, a.epc);
+    if (g >= Ge) return;
+    const int c0 = (int)(((long long)n * g) / Ge), c1 = (int)(((long long)n * (g + 1)) / Ge);
     const int w = c1 - c0;
-    const int wmax = (a.nmax + G - 1) / G;
     const int mmax = a.mmax;
 
-    T* lcol = reinterpret_cast<T*>(smem_raw);           // [mmax] multipliers S[r, j] / pivot
-    T* prow = lcol + mmax;                               // [wmax] pivot row, own columns
-    double* skey = reinterpret_cast<double*>(prow + wmax);  // [NWARP + 1]
-    int* slin = reinterpret_cast<int*>(skey + NWARP + 1);   // [NWARP + 1]
-    int* sint = slin + NWARP + 1;                           // [4] flags
-    unsigned char* rowused = reinterpret_cast<unsigned char*>(sint + 4);  // [mmax]
-    unsigned char* colused = rowused + mmax;                              // [wmax]
+    // shared memory: [W block] lcol[mmax] prow[wcols] sval[G] | skey slin sint | rowused colused
+    T* Wsm = reinterpret_cast<T*>(smem_raw);
+    T* lcol = Wsm + (SMEMW ? a.wcap_elems : 0);
+    T* prow = lcol + mmax;
+    T* sval = prow + a.wcap_cols;
+    Decision<T>* dec = align16<Decision<T>>(sval + G);
+    kbits_t* skey = reinterpret_cast<kbits_t*>(dec + 1);
+    int* slin = reinterpret_cast<int*>(skey + NWARP + 1);
+    int* sint = slin + NWARP + 1;
+    unsigned char* rowused = reinterpret_cast<unsigned char*>(sint + 4);
+    unsigned char* colused = rowused + mmax;
 
-    T* Wb = a.W + (size_t)c0 * mmax;
-
-    for (int e = tid; e < m * w; e += PT) {
-        const int r = e / w, cc = e % w;
-        Wb[(size_t)cc * mmax + r] = a.Min[(size_t)r * n + c0 + cc];
+    T* Wb;
+    int ldw;
+    if (SMEMW) {
+        Wb = Wsm;
+        ldw = m;
+    } else {
+        Wb = a.W + (size_t)c0 * mmax;
+        ldw = mmax;
     }
-    for (int r = tid; r < m; r += PT) rowused[r] = 0;
+    unsigned long long* recs = a.ll;                                  // [2][G][kRecWords]
+    unsigned long long* cols = a.ll + 2 * (size_t)G * kRecWords;      // [2][G][mmax * WPV]
+
+    // Copy the own column block (thread = row) and find the first local candidate.
+    kbits_t bkey = 0;
+    int blin = INT_MAX;
+    for (int r = tid; r < m; r += PT) {
+        rowused[r] = 0;
+        const T* src = a.Min + (size_t)r * n + c0;
+        const int rn = r * n + c0;
+        for (int cc = 0; cc < w; ++cc) {
+            const T v = src[cc];
+            Wb[(size_t)cc * ldw + r] = v;
+            const kbits_t k = key_of(v);
+            if (better(k, rn + cc, bkey, blin)) { bkey = k; blin = rn + cc; }
+        }
+    }
     for (int cc = tid; cc < w; cc += PT) colused[cc] = 0;
     if (tid < 4) sint[tid] = 0;
     __syncthreads();
@@ -115,145 +235,133 @@ __global__ void __launch_bounds__(PT) prrlu_kernel(PrrluArgs<T> a) {
     const double S = a.rel ? __longlong_as_double((long long)*a.smax) : 0.0;
     const double tau = a.rel ? a.tol * S : a.tol;
 
-    double bkey = -1.0;
-    int blin = INT_MAX;
-    for (int e = tid; e < m * w; e += PT) {
-        const int cc = e / m, r = e - cc * m;
-        const double k = sanitize_key(s_key(Wb[(size_t)cc * mmax + r]));
-        const int lin = r * n + c0 + cc;
-        if (better(k, lin, bkey, blin)) { bkey = k; blin = lin; }
-    }
-
     int p = 0;
     double eps = 0.0;
     for (;;) {
         block_argmax(bkey, blin, skey, slin);
+        const unsigned int tag = a.tagbase + (unsigned int)(p + 1);
         const int buf = p & 1;
-        PivRec* myrec = a.rec + (size_t)buf * G + g;
-        T* myslot = a.slots + ((size_t)buf * G + g) * mmax;
-        if (blin != INT_MAX) {
-            const int cc = (blin % n) - c0;
-            for (int r = tid; r < m; r += PT) myslot[r] = Wb[(size_t)cc * mmax + r];
-        }
-        __syncthreads();
-        const unsigned long long tag = (a.epoch << 24) | (unsigned long long)(p + 1);
-        if (tid == 0) {
+        kbits_t wkey = bkey;
+        int wlin = blin;
+        T piv = s_zero(T());
+        int gw = g;  // CTA that owns the winning column
+        if (Ge == 1) {
+            if (wlin != INT_MAX) piv = Wb[(size_t)(wlin % n - c0) * ldw + wlin / n];
+        } else {
+            // publish: candidate column and record, as tagged words (no fence needed)
+            unsigned long long* myrec = recs + ((size_t)buf * G + g) * kRecWords;
+            unsigned long long* mycol = cols + ((size_t)buf * G + g) * (size_t)mmax * WPV;
             if (blin != INT_MAX) {
-                const int r = blin / n, c = blin % n;
-                myrec->key = bkey;
-                set_val(myrec, Wb[(size_t)(c - c0) * mmax + r]);
-                myrec->r = r;
-                myrec->c = c;
-            } else {
-                myrec->key = -1.0;
-                set_val(myrec, s_zero(T()));
-                myrec->r = -1;
-                myrec->c = -1;
+                const T* colp = Wb + (size_t)(blin % n - c0) * ldw;
+                for (int r = tid; r < m; r += PT) put_val(mycol + (size_t)r * WPV, colp[r], tag);
             }
-            __threadfence();
-            st_release_u64(&myrec->tag, tag);
-        }
-        // One grid-wide synchronisation per step: wait for the G records of this step.
-        if (tid < G) {
-            const PivRec* rr = a.rec + (size_t)buf * G + tid;
-            long long spins = 0;
-            while (ld_acquire_u64(&rr->tag) != tag) {
-                if (++spins > kSpinLimit) {
+            if (tid == 0) {
+                st_word(myrec, (unsigned int)(bkey >> 32), tag);
+                st_word(myrec + 1, (unsigned int)bkey, tag);
+                st_word(myrec + 2, (unsigned int)blin, tag);
+                T v = s_zero(T());
+                if (blin != INT_MAX) v = Wb[(size_t)(blin % n - c0) * ldw + blin / n];
+                put_val(myrec + 3, v, tag);
+            }
+            // gather the Ge records of this step (one poller per record)
+            wkey = 0;
+            wlin = INT_MAX;
+            if (tid < Ge) {
+                unsigned long long rw[3 + WPV];
+                if (!get_words<3 + WPV>(recs + ((size_t)buf * G + tid) * kRecWords, tag, rw)) {
                     atomicOr(a.err, DEVERR_TIMEOUT);
                     sint[0] = 1;
-                    break;
+                } else {
+                    wkey = ((kbits_t)word_data(rw[0]) << 32) | word_data(rw[1]);
+                    wlin = (int)word_data(rw[2]);
+                    T v;
+                    val_of(rw + 3, v);
+                    sval[tid] = v;
                 }
             }
-        }
-        __threadfence();
-        __syncthreads();
-        if (sint[0]) return;  // gave up waiting; the host reads ACI_E_TIMEOUT
-
-        double wkey = -1.0;
-        int wlin = INT_MAX;
-        if (tid < G) {
-            const PivRec* rr = a.rec + (size_t)buf * G + tid;
-            const int r = ldcg(&rr->r);
-            if (r >= 0) {
-                wkey = __ldcg(&rr->key);
-                wlin = r * n + ldcg(&rr->c);
+            block_argmax(wkey, wlin, skey, slin);
+            if (sint[0]) return;  // gave up waiting; the host reads ACI_E_TIMEOUT
+            if (wlin != INT_MAX) {
+                const int cj = wlin % n;
+                gw = (int)((((long long)cj + 1) * Ge - 1) / n);
+                piv = sval[gw];
             }
         }
-        const int mylin = wlin;
-        block_argmax(wkey, wlin, skey, slin);
-        if (tid < G && mylin == wlin && wlin != INT_MAX) sint[1] = tid;
+        if (tid == 0) decide(dec, wkey, wlin, piv, p, kmax, tau);
         __syncthreads();
-        if (wlin == INT_MAX) {  // no unused entry is left
-            eps = 0.0;
+        if (dec->code) {  // stop: no unused entry left, tolerance or rank cap reached, or non-finite
+            if (dec->code == 2 && g == 0 && tid == 0) atomicOr(a.err, DEVERR_NUMERIC);
+            eps = dec->eps;
             break;
         }
-        const double mag = key_to_mag(wkey, T());
-        if (!(wkey < INFINITY)) {
-            if (g == 0 && tid == 0) atomicOr(a.err, DEVERR_NUMERIC);
-            eps = mag;
-            break;
-        }
-        if (p == kmax || (p >= 1 && mag <= tau)) {
-            eps = mag;
-            break;
-        }
-        const int wi = sint[1];
-        const PivRec* wr = a.rec + (size_t)buf * G + wi;
-        T piv;
-        get_val(wr, piv);
         const int ri = wlin / n, cj = wlin % n;
-        const bool zpiv = s_iszero(piv);
+        const bool zpiv = dec->zpiv;
+        const T inv = dec->inv;
         if (g == 0 && tid == 0) {
             a.piv_rows[p] = ri;
             a.piv_cols[p] = cj;
             a.D[p] = piv;
         }
-        const T* wslot = a.slots + ((size_t)buf * G + wi) * mmax;
-        for (int r = tid; r < m; r += PT) {
-            T l = s_zero(T());
-            if (!rowused[r] && r != ri && !zpiv) l = s_div(ldcg(wslot + r), piv);
-            lcol[r] = l;
-        }
-        if (a.L) {  // column p of L, rows split across the CTAs
-            const int r0 = (int)(((long long)m * g) / G), r1 = (int)(((long long)m * (g + 1)) / G);
-            for (int r = r0 + tid; r < r1; r += PT) {
+        // Multipliers S[r, cj] / pivot from the winning column; pivot row of the own columns.
+        // Row ri and column cj become used here; the loops below never read those flags for them.
+        if (Ge == 1) {
+            const T* colp = Wb + (size_t)(cj - c0) * ldw;
+            for (int r = tid; r < m; r += PT)
+                lcol[r] = (rowused[r] || r == ri || zpiv) ? s_zero(T()) : s_mul(colp[r], inv);
+        } else {
+            const unsigned long long* wc = cols + ((size_t)buf * G + gw) * (size_t)mmax * WPV;
+            for (int r = tid; r < m; r += PT) {
+                unsigned long long cw[WPV];
+                if (!get_words<WPV>(wc + (size_t)r * WPV, tag, cw)) {
+                    atomicOr(a.err, DEVERR_TIMEOUT);
+                    sint[1] = 1;
+                    break;
+                }
                 T v;
-                if (r == ri) v = s_one(T());
-                else if (rowused[r] || zpiv) v = s_zero(T());
-                else v = s_div(ldcg(wslot + r), piv);
-                a.L[(size_t)p * a.Lld + r] = v;
+                val_of(cw, v);
+                lcol[r] = (rowused[r] || r == ri || zpiv) ? s_zero(T()) : s_mul(v, inv);
             }
         }
         for (int cc = tid; cc < w; cc += PT) {
-            const T v = Wb[(size_t)cc * mmax + ri];
+            const T v = Wb[(size_t)cc * ldw + ri];
             prow[cc] = v;
             if (a.U) {
                 const int c = c0 + cc;
                 T u;
                 if (c == cj) u = s_one(T());
                 else if (colused[cc] || zpiv) u = s_zero(T());
-                else u = s_div(v, piv);
+                else u = s_mul(v, inv);
                 a.U[(size_t)p * a.Uld + c] = u;
             }
         }
         __syncthreads();
+        if (sint[1]) return;
         if (tid == 0) {
             rowused[ri] = 1;
             if (cj >= c0 && cj < c1) colused[cj - c0] = 1;
         }
+        if (a.L) {  // column p of L, rows split across the CTAs
+            const int r0 = (int)(((long long)m * g) / Ge), r1 = (int)(((long long)m * (g + 1)) / Ge);
+            for (int r = r0 + tid; r < r1; r += PT) a.L[(size_t)p * a.Lld + r] = (r == ri) ? s_one(T()) : lcol[r];
+        }
         __syncthreads();
-        // Schur-complement update of the unused block, fused with the next local argmax.
-        bkey = -1.0;
+        // Schur-complement update of the unused block (thread = row), fused with the next
+        // local argmax.
+        bkey = 0;
         blin = INT_MAX;
-        for (int e = tid; e < m * w; e += PT) {
-            const int cc = e / m, r = e - cc * m;
-            if (rowused[r] | colused[cc]) continue;
-            T* ptr = Wb + (size_t)cc * mmax + r;
-            const T v = s_fms(lcol[r], prow[cc], *ptr);
-            *ptr = v;
-            const double k = sanitize_key(s_key(v));
-            const int lin = r * n + c0 + cc;
-            if (better(k, lin, bkey, blin)) { bkey = k; blin = lin; }
+        for (int r = tid; r < m; r += PT) {
+            if (rowused[r]) continue;
+            const T l = lcol[r];
+            const int rn = r * n + c0;
+            T* rowp = Wb + r;
+            for (int cc = 0; cc < w; ++cc) {
+                if (colused[cc]) continue;
+                T* ptr = rowp + (size_t)cc * ldw;
+                const T v = s_fms(l, prow[cc], *ptr);
+                *ptr = v;
+                const kbits_t k = key_of(v);
+                if (better(k, rn + cc, bkey, blin)) { bkey = k; blin = rn + cc; }
+            }
         }
         ++p;
     }
@@ -270,41 +378,589 @@ __global__ void __launch_bounds__(PT) prrlu_kernel(PrrluArgs<T> a) {
     }
 }
 
-}  // namespace
+// ---------------------------------------------------------------- cluster variant
+// For blocks that 16 SMs of FP64 can update fast enough (the usual case), the CTAs of one
+// thread-block cluster share the work and exchange through distributed shared memory: every
+// step, each CTA writes its best candidate into every CTA's candidate slots, one hardware
+// cluster barrier (release/acquire) follows, each CTA reduces the C candidates locally, and
+// reads the winning column straight out of the owner's shared memory (a pivot column is never
+// written again once chosen). No L2 round trip and no software spin is on the step's path.
+template <class T> struct __align__(16) Cand {
+    kbits_t key;
+    int lin;
+    int pad;
+    T val;
+};
 
-int prrlu_grid(int nmax, int num_sms) {
-    int G = nmax / 4;
-    if (G < 1) G = 1;
-    if (G > num_sms) G = num_sms;
-    if (G > PT) G = PT;  // one waiting thread per record
-    return G;
+template <class T, bool SMEMW>
+__global__ void __launch_bounds__(PT) prrlu_cluster_kernel(PrrluArgs<T> a) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int g = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m = dimv(a.m, a.chi), n = dimv(a.n, a.chi);
+    const int c0 = (int)(((long long)n * g) / C), c1 = (int)(((long long)n * (g + 1)) / C);
+    const int w = c1 - c0;
+    const int mmax = a.mmax;
+
+    // shared memory: [W block] lcol[mmax] prow[wcols] cand[2][C] | wbest | rowused colused
+    T* Wsm = reinterpret_cast<T*>(smem_raw);
+    T* lcol = Wsm + (SMEMW ? a.wcap_elems : 0);
+    T* prow = lcol + mmax;
+    Cand<T>* cand = align16<Cand<T>>(prow + a.wcap_cols);            // [2][C]
+    Cand<T>* wbest = cand + 2 * C;                                    // [NWARP + 1]
+    Decision<T>* dec = reinterpret_cast<Decision<T>*>(wbest + NWARP + 1);
+    unsigned char* rowused = reinterpret_cast<unsigned char*>(dec + 1);
+    unsigned char* colused = rowused + mmax;
+
+    T* Wb;
+    int ldw;
+    if (SMEMW) {
+        Wb = Wsm;
+        ldw = m;
+    } else {
+        Wb = a.W + (size_t)c0 * mmax;
+        ldw = mmax;
+    }
+
+    kbits_t bkey = 0;
+    int blin = INT_MAX;
+    for (int r = tid; r < m; r += PT) {
+        rowused[r] = 0;
+        const T* src = a.Min + (size_t)r * n + c0;
+        const int rn = r * n + c0;
+        for (int cc = 0; cc < w; ++cc) {
+            const T v = src[cc];
+            Wb[(size_t)cc * ldw + r] = v;
+            const kbits_t k = key_of(v);
+            if (better(k, rn + cc, bkey, blin)) { bkey = k; blin = rn + cc; }
+        }
+    }
+    for (int cc = tid; cc < w; cc += PT) colused[cc] = 0;
+    __syncthreads();
+
+    const int kmax = min(min(m, n), a.chimax);
+    const double S = a.rel ? __longlong_as_double((long long)*a.smax) : 0.0;
+    const double tau = a.rel ? a.tol * S : a.tol;
+
+    int p = 0;
+    double eps = 0.0;
+    for (;;) {
+        const int par = p & 1;
+        // (1) CTA best: warp reductions, then warp 0 reduces the warp bests and broadcasts the
+        //     CTA's candidate into slot [par][g] of every CTA of the cluster.
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const kbits_t ok = __shfl_xor_sync(0xffffffffu, bkey, off);
+            const int ol = __shfl_xor_sync(0xffffffffu, blin, off);
+            if (better(ok, ol, bkey, blin)) { bkey = ok; blin = ol; }
+        }
+        if (lane == 0) { wbest[warp].key = bkey; wbest[warp].lin = blin; }
+        __syncthreads();
+        if (warp == 0) {
+            kbits_t k = lane < NWARP ? wbest[lane].key : 0ull;
+            int l = lane < NWARP ? wbest[lane].lin : INT_MAX;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const kbits_t ok = __shfl_xor_sync(0xffffffffu, k, off);
+                const int ol = __shfl_xor_sync(0xffffffffu, l, off);
+                if (better(ok, ol, k, l)) { k = ok; l = ol; }
+            }
+            Cand<T> mine;
+            mine.key = k;
+            mine.lin = l;
+            mine.pad = 0;
+            mine.val = (l != INT_MAX) ? Wb[(size_t)(l % n - c0) * ldw + l / n] : s_zero(T());
+            for (int t = lane; t < C; t += 32) *cl.map_shared_rank(cand + par * C + g, t) = mine;
+        }
+        cl.sync();
+        // (2) winner among the C candidates (warp 0), broadcast through wbest[NWARP]
+        if (warp == 0) {
+            kbits_t k = 0;
+            int l = INT_MAX, src = 0;
+            for (int t = lane; t < C; t += 32) {
+                const Cand<T>& c = cand[par * C + t];
+                if (better(c.key, c.lin, k, l)) { k = c.key; l = c.lin; src = t; }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const kbits_t ok = __shfl_xor_sync(0xffffffffu, k, off);
+                const int ol = __shfl_xor_sync(0xffffffffu, l, off);
+                const int os = __shfl_xor_sync(0xffffffffu, src, off);
+                if (better(ok, ol, k, l)) { k = ok; l = ol; src = os; }
+            }
+            if (lane == 0) {
+                const T pv = cand[par * C + src].val;
+                wbest[NWARP].key = k;
+                wbest[NWARP].lin = l;
+                wbest[NWARP].pad = src;
+                wbest[NWARP].val = pv;
+                decide(dec, k, l, pv, p, kmax, tau);
+            }
+        }
+        __syncthreads();
+        const int wlin = wbest[NWARP].lin;
+        const int gw = wbest[NWARP].pad;
+        const T piv = wbest[NWARP].val;
+        if (dec->code) {  // stop: no unused entry left, tolerance or rank cap reached, or non-finite
+            if (dec->code == 2 && g == 0 && tid == 0) atomicOr(a.err, DEVERR_NUMERIC);
+            eps = dec->eps;
+            break;
+        }
+        const int ri = wlin / n, cj = wlin % n;
+        const bool zpiv = dec->zpiv;
+        const T inv = dec->inv;
+        if (g == 0 && tid == 0) {
+            a.piv_rows[p] = ri;
+            a.piv_cols[p] = cj;
+            a.D[p] = piv;
+        }
+        // (3) multipliers from the winning column, read from its owner (never written again)
+        {
+            const T* colp;
+            if (SMEMW) {
+                const int c0w = (int)(((long long)n * gw) / C);
+                colp = cl.map_shared_rank(Wsm, gw) + (size_t)(cj - c0w) * m;
+            } else {
+                colp = a.W + (size_t)cj * mmax;
+            }
+            for (int r = tid; r < m; r += PT) {
+                T v;
+                if (SMEMW) v = colp[r];
+                else v = ldcg_val(colp + r);
+                lcol[r] = (rowused[r] || r == ri || zpiv) ? s_zero(T()) : s_mul(v, inv);
+            }
+        }
+        for (int cc = tid; cc < w; cc += PT) {
+            const T v = Wb[(size_t)cc * ldw + ri];
+            prow[cc] = v;
+            if (a.U) {
+                const int c = c0 + cc;
+                T u;
+                if (c == cj) u = s_one(T());
+                else if (colused[cc] || zpiv) u = s_zero(T());
+                else u = s_mul(v, inv);
+                a.U[(size_t)p * a.Uld + c] = u;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            rowused[ri] = 1;
+            if (cj >= c0 && cj < c1) colused[cj - c0] = 1;
+        }
+        if (a.L) {  // column p of L, rows split across the CTAs
+            const int r0 = (int)(((long long)m * g) / C), r1 = (int)(((long long)m * (g + 1)) / C);
+            for (int r = r0 + tid; r < r1; r += PT) a.L[(size_t)p * a.Lld + r] = (r == ri) ? s_one(T()) : lcol[r];
+        }
+        __syncthreads();
+        // (4) Schur-complement update (thread = row), fused with the next local argmax
+        bkey = 0;
+        blin = INT_MAX;
+        for (int r = tid; r < m; r += PT) {
+            if (rowused[r]) continue;
+            const T l = lcol[r];
+            const int rn = r * n + c0;
+            T* rowp = Wb + r;
+            for (int cc = 0; cc < w; ++cc) {
+                if (colused[cc]) continue;
+                T* ptr = rowp + (size_t)cc * ldw;
+                const T v = s_fms(l, prow[cc], *ptr);
+                *ptr = v;
+                const kbits_t k = key_of(v);
+                if (better(k, rn + cc, bkey, blin)) { bkey = k; blin = rn + cc; }
+            }
+        }
+        ++p;
+    }
+    if (g == 0 && tid == 0) {
+        if (a.flops) {
+            const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
+            double f = 0.0;
+            for (int q = 0; q < p; ++q) f += (double)(m - q - 1) * (double)(n - q - 1);
+            atomicAdd(a.flops, per * f);
+        }
+        *a.eps_out = eps;
+        if (a.k_out) *a.k_out = p;
+        if (a.out_chi_idx >= 0) const_cast<int*>(a.chi)[a.out_chi_idx] = p;
+    }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// ---------------------------------------------------------------- register-resident cluster variant
+// The usual case (cluster sizes up to 16, m <= 1024 rows, at most 32 columns per CTA): each of
+// the 512 threads keeps its rows' slice of the CTA's columns in registers, so the Schur update
+// is a run of independent FP64 multiply-adds with no shared-memory traffic. Per step:
+//   warp maxima -> shared -> every warp reduces them (no broadcast barrier);
+//   the CTA writes its candidate column to shared memory and its candidate (key, position,
+//   value) into every CTA's slot; one cluster barrier; every warp reduces the C candidates;
+//   each thread reads its rows' entries of the winning column from the owner's shared memory;
+//   the thread holding the pivot row publishes it; one block barrier; update.
+constexpr int RT = 512;
+constexpr int RWARP = RT / 32;
+
+__device__ __forceinline__ double shfl_x(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ cplx shfl_x(cplx v, int off) {
+    return mkc(__shfl_xor_sync(0xffffffffu, v.re, off), __shfl_xor_sync(0xffffffffu, v.im, off));
+}
+__device__ __forceinline__ double shfl_0(double v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ cplx shfl_0(cplx v) {
+    return mkc(__shfl_sync(0xffffffffu, v.re, 0), __shfl_sync(0xffffffffu, v.im, 0));
 }
 
 template <class T>
-size_t prrlu_smem_bytes(int mmax, int nmax, int G) {
-    const int wmax = (nmax + G - 1) / G;
-    size_t b = sizeof(T) * (size_t)(mmax + wmax);
-    b += sizeof(double) * (NWARP + 1) + sizeof(int) * (NWARP + 1) + sizeof(int) * 4;
-    b += (size_t)mmax + (size_t)wmax;
+__device__ __forceinline__ void warp_best(kbits_t& k, int& l, T& v, int& s) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const kbits_t ok = __shfl_xor_sync(0xffffffffu, k, off);
+        const int ol = __shfl_xor_sync(0xffffffffu, l, off);
+        const T ov = shfl_x(v, off);
+        const int os = __shfl_xor_sync(0xffffffffu, s, off);
+        if (better(ok, ol, k, l)) { k = ok; l = ol; v = ov; s = os; }
+    }
+}
+
+template <class T, int ROWS, int WMAX>
+__global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int g = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m = dimv(a.m, a.chi), n = dimv(a.n, a.chi);
+    const int c0 = (int)(((long long)n * g) / C), c1 = (int)(((long long)n * (g + 1)) / C);
+    const int w = c1 - c0;  // <= WMAX (the host sizes WMAX for the capacity)
+    const int mmax = a.mmax;
+
+    // shared memory: candcol[2][mmax] | prow[WMAX] | cand[2][C] | warp maxima
+    T* candcol = reinterpret_cast<T*>(smem_raw);
+    T* prow = candcol + 2 * (size_t)mmax;
+    Cand<T>* cand = align16<Cand<T>>(prow + WMAX);
+    Cand<T>* wmx = cand + 2 * C;  // [RWARP]
+
+    T v[ROWS][WMAX];
+    bool live[ROWS];
+    kbits_t bkey = 0;
+    int blin = INT_MAX;
+    T bval = s_zero(T());
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i) {
+        const int r = tid + i * RT;
+        live[i] = r < m;
+        const T* src = a.Min + (size_t)r * n + c0;
+#pragma unroll
+        for (int cc = 0; cc < WMAX; ++cc) {
+            T x = s_zero(T());
+            if (live[i] && cc < w) {
+                x = src[cc];
+                const kbits_t k = key_of(x);
+                if (better(k, r * n + c0 + cc, bkey, blin)) { bkey = k; blin = r * n + c0 + cc; bval = x; }
+            }
+            v[i][cc] = x;
+        }
+    }
+    unsigned int colmask = (w >= 32) ? 0xFFFFFFFFu : ((1u << w) - 1u);
+
+    const int kmax = min(min(m, n), a.chimax);
+    const double S = a.rel ? __longlong_as_double((long long)*a.smax) : 0.0;
+    const double tau = a.rel ? a.tol * S : a.tol;
+
+    int p = 0;
+    double eps = 0.0;
+    for (;;) {
+        const int par = p & 1;
+        // (1) the CTA's candidate
+        int dummy = 0;
+        warp_best(bkey, blin, bval, dummy);
+        if (lane == 0) {
+            wmx[warp].key = bkey;
+            wmx[warp].lin = blin;
+            wmx[warp].val = bval;
+        }
+        __syncthreads();
+        kbits_t ck = 0;
+        int cl_ = INT_MAX, cs = 0;
+        T cv = s_zero(T());
+        if (lane < RWARP) { ck = wmx[lane].key; cl_ = wmx[lane].lin; cv = wmx[lane].val; }
+        warp_best(ck, cl_, cv, cs);
+        const int ccb = (cl_ != INT_MAX) ? (cl_ % n - c0) : -1;
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+            const int r = tid + i * RT;
+            if (r < m) {
+                T x = s_zero(T());
+#pragma unroll
+                for (int cc = 0; cc < WMAX; ++cc)
+                    if (cc == ccb) x = v[i][cc];
+                candcol[(size_t)par * mmax + r] = x;
+            }
+        }
+        if (warp == 0) {
+            Cand<T> mine;
+            mine.key = ck;
+            mine.lin = cl_;
+            mine.pad = 0;
+            mine.val = cv;
+            for (int t = lane; t < C; t += 32) *cl.map_shared_rank(cand + par * C + g, t) = mine;
+        }
+        cl.sync();
+        // (2) the winner among the C candidates, and the step's decision (every warp)
+        kbits_t wk = 0;
+        int wl = INT_MAX, gw = 0;
+        T pv = s_zero(T());
+        for (int t = lane; t < C; t += 32) {
+            const Cand<T>& c = cand[par * C + t];
+            if (better(c.key, c.lin, wk, wl)) { wk = c.key; wl = c.lin; pv = c.val; gw = t; }
+        }
+        warp_best(wk, wl, pv, gw);
+        int code = 0, zpiv = 0;
+        double de = 0.0;
+        T inv = s_zero(T());
+        if (lane == 0) {
+            Decision<T> d;
+            decide(&d, wk, wl, pv, p, kmax, tau);
+            code = d.code;
+            zpiv = d.zpiv;
+            de = d.eps;
+            inv = d.inv;
+        }
+        code = __shfl_sync(0xffffffffu, code, 0);
+        if (code) {
+            if (code == 2 && g == 0 && tid == 0) atomicOr(a.err, DEVERR_NUMERIC);
+            eps = shfl_0(de);
+            break;
+        }
+        zpiv = __shfl_sync(0xffffffffu, zpiv, 0);
+        inv = shfl_0(inv);
+        const int ri = wl / n, cj = wl % n;
+        if (g == 0 && tid == 0) {
+            a.piv_rows[p] = ri;
+            a.piv_cols[p] = cj;
+            a.D[p] = pv;
+        }
+        // (3) multipliers of the own rows, from the owner's candidate column
+        const T* wcol = cl.map_shared_rank(candcol + (size_t)par * mmax, gw);
+        T l[ROWS];
+        const int r0 = (int)(((long long)m * g) / C), r1 = (int)(((long long)m * (g + 1)) / C);
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+            const int r = tid + i * RT;
+            l[i] = s_zero(T());
+            if (live[i] && r != ri && !zpiv) l[i] = s_mul(wcol[r], inv);
+            if (a.L && r >= r0 && r < r1) a.L[(size_t)p * a.Lld + r] = (r == ri) ? s_one(T()) : l[i];
+            if (r == ri) {  // this thread holds the pivot row: publish it and row p of U
+#pragma unroll
+                for (int cc = 0; cc < WMAX; ++cc) {
+                    prow[cc] = v[i][cc];
+                    if (a.U && cc < w) {
+                        T u;
+                        if (c0 + cc == cj) u = s_one(T());
+                        else if (!((colmask >> cc) & 1u) || zpiv) u = s_zero(T());
+                        else u = s_mul(v[i][cc], inv);
+                        a.U[(size_t)p * a.Uld + c0 + cc] = u;
+                    }
+                }
+                live[i] = false;
+            }
+        }
+        if (cj >= c0 && cj < c1) colmask &= ~(1u << (cj - c0));
+        __syncthreads();
+        // (4) Schur-complement update in registers, fused with the next local argmax
+        bkey = 0;
+        blin = INT_MAX;
+        bval = s_zero(T());
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+            if (!live[i]) continue;
+            const int rn = (tid + i * RT) * n + c0;
+#pragma unroll
+            for (int cc = 0; cc < WMAX; ++cc) {
+                if ((colmask >> cc) & 1u) {
+                    const T x = s_fms(l[i], prow[cc], v[i][cc]);
+                    v[i][cc] = x;
+                    const kbits_t k = key_of(x);
+                    if (better(k, rn + cc, bkey, blin)) { bkey = k; blin = rn + cc; bval = x; }
+                }
+            }
+        }
+        ++p;
+    }
+    if (g == 0 && tid == 0) {
+        if (a.flops) {
+            const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
+            double f = 0.0;
+            for (int q = 0; q < p; ++q) f += (double)(m - q - 1) * (double)(n - q - 1);
+            atomicAdd(a.flops, per * f);
+        }
+        *a.eps_out = eps;
+        if (a.k_out) *a.k_out = p;
+        if (a.out_chi_idx >= 0) const_cast<int*>(a.chi)[a.out_chi_idx] = p;
+    }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+template <class T>
+size_t creg_bytes(int mmax, int C, int wmax) {
+    size_t b = sizeof(T) * (2 * (size_t)mmax + wmax);
+    b = (b + 15) & ~(size_t)15;
+    b += sizeof(Cand<T>) * (2 * (size_t)C + RWARP);
+    return b;
+}
+
+constexpr size_t kSmemLimit = 200 * 1024;
+
+template <class T>
+size_t layout_bytes(int mmax, int G, int wcap_elems, int wcap_cols, bool smemw) {
+    size_t b = sizeof(T) * ((smemw ? (size_t)wcap_elems : 0) + mmax + wcap_cols + G);
+    b = (b + 15) & ~(size_t)15;
+    b += sizeof(Decision<T>);
+    b += sizeof(unsigned long long) * (NWARP + 1) + sizeof(int) * (NWARP + 1) + sizeof(int) * 4;
+    b += (size_t)mmax + (size_t)wcap_cols;
     return (b + 15) & ~(size_t)15;
 }
 
+}  // namespace
+
+// Target entries per CTA; ACI_PRRLU_EPC overrides it (launch-shape tuning only).
+int prrlu_epc() {
+    static const int v = [] {
+        const char* e = std::getenv("ACI_PRRLU_EPC");
+        const int x = e ? std::atoi(e) : 0;
+        return x > 0 ? x : kPrrluEpc;
+    }();
+    return v;
+}
+
+int prrlu_grid(int mmax, int nmax, int num_sms) {
+    return live_ctas((long long)mmax * nmax, nmax, std::min(num_sms, PT), prrlu_epc());
+}
+
+size_t prrlu_ll_words(int mmax, int G, bool cplx_values) {
+    const int wpv = cplx_values ? 4 : 2;
+    return 2 * (size_t)G * kRecWords + 2 * (size_t)G * mmax * wpv;
+}
+
+// Shared-memory bytes of the cluster kernel.
 template <class T>
-cudaError_t launch_prrlu(const PrrluArgs<T>& a, int G, cudaStream_t st) {
-    const size_t smem = prrlu_smem_bytes<T>(a.mmax, a.nmax, G);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(prrlu_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
+size_t cluster_bytes(int mmax, int C, int wcap_elems, int wcap_cols, bool smemw) {
+    size_t b = sizeof(T) * ((smemw ? (size_t)wcap_elems : 0) + mmax + wcap_cols);
+    b = (b + 15) & ~(size_t)15;
+    b += sizeof(Cand<T>) * (2 * (size_t)C + NWARP + 1) + sizeof(Decision<T>);
+    b += (size_t)mmax + (size_t)wcap_cols;
+    return (b + 15) & ~(size_t)15;
+}
+
+// Largest cluster (16, else 8) the device can schedule for the cluster kernel.
+template <class T>
+int max_cluster() {
+    static int v = 0;
+    if (v) return v;
+    v = 8;
+    auto fn = prrlu_cluster_kernel<T, true>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit) == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(PT);
+        cfg.dynamicSmemBytes = kSmemLimit;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, (void*)fn, &cfg) == cudaSuccess && n >= 1) v = 16;
     }
-    PrrluArgs<T> copy = a;
-    void* args[] = {&copy};
-    return cudaLaunchCooperativeKernel((const void*)prrlu_kernel<T>, dim3(G), dim3(PT), args, smem, st);
+    cudaGetLastError();
+    return v;
+}
+
+// Blocks whose FP64 update work (entries, x4 for complex) is at most this run in one cluster.
+constexpr long long kClusterWorkMax = 1LL << 18;
+
+template <class T>
+cudaError_t launch_prrlu(const PrrluArgs<T>& a_in, int G, cudaStream_t st) {
+    PrrluArgs<T> a = a_in;
+    const bool cp = sizeof(T) == sizeof(cplx);
+    const long long work = (long long)a.mmax * a.nmax * (cp ? 4 : 1);
+    if (work <= kClusterWorkMax) {
+        const int cmax = max_cluster<T>();
+        int C = (int)std::min<long long>(cmax, std::max(1LL, (work + 4095) / 4096));
+        C = std::max(C, std::min(cmax, (a.nmax + 31) / 32));  // at most 32 columns per CTA if possible
+        C = std::max(1, std::min(C, a.nmax));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(C);
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const int wneed = (a.nmax + C - 1) / C;
+        const int rows = (a.mmax + RT - 1) / RT;
+        void (*reg)(PrrluArgs<T>) = nullptr;
+        int wmax = 0;
+        // register budget: at most 32 values per thread (real) or 16 (complex)
+        if (rows == 1) {
+            if (wneed <= 8) { reg = prrlu_creg_kernel<T, 1, 8>; wmax = 8; }
+            else if (wneed <= 16) { reg = prrlu_creg_kernel<T, 1, 16>; wmax = 16; }
+            else if constexpr (sizeof(T) == sizeof(double)) {
+                if (wneed <= 32) { reg = prrlu_creg_kernel<T, 1, 32>; wmax = 32; }
+            }
+        } else if (rows == 2) {
+            if (wneed <= 8) { reg = prrlu_creg_kernel<T, 2, 8>; wmax = 8; }
+            else if constexpr (sizeof(T) == sizeof(double)) {
+                if (wneed <= 16) { reg = prrlu_creg_kernel<T, 2, 16>; wmax = 16; }
+            }
+        }
+        if (reg) {
+            a.epc = 0;
+            a.wcap_cols = wmax;
+            a.wcap_elems = 0;
+            const size_t smem = creg_bytes<T>(a.mmax, C, wmax);
+            cudaError_t e = cudaFuncSetAttribute(reg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+            if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute(reg, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+            cfg.blockDim = dim3(RT);
+            cfg.dynamicSmemBytes = smem;
+            return cudaLaunchKernelEx(&cfg, reg, a);
+        }
+        a.epc = 0;
+        a.wcap_cols = wneed;
+        a.wcap_elems = a.mmax * a.wcap_cols;
+        const bool smemw = cluster_bytes<T>(a.mmax, C, a.wcap_elems, a.wcap_cols, true) <= kSmemLimit;
+        const size_t smem = cluster_bytes<T>(a.mmax, C, a.wcap_elems, a.wcap_cols, smemw);
+        if (smem > kSmemLimit) return cudaErrorInvalidValue;
+        void (*fn)(PrrluArgs<T>) = smemw ? prrlu_cluster_kernel<T, true> : prrlu_cluster_kernel<T, false>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+        if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        cfg.blockDim = dim3(PT);
+        cfg.dynamicSmemBytes = smem;
+        return cudaLaunchKernelEx(&cfg, fn, a);
+    }
+    a.epc = prrlu_epc();
+    // worst-case block over every live shape this launch may meet (see live_ctas)
+    const int ceil_n = (a.nmax + G - 1) / G;
+    a.wcap_elems = std::max(a.epc + a.mmax, a.mmax * ceil_n);
+    a.wcap_cols = std::min(a.nmax, std::max(ceil_n, a.epc));
+    const bool smemw = layout_bytes<T>(a.mmax, G, a.wcap_elems, a.wcap_cols, true) <= kSmemLimit;
+    const size_t smem = layout_bytes<T>(a.mmax, G, a.wcap_elems, a.wcap_cols, smemw);
+    if (smem > kSmemLimit) return cudaErrorInvalidValue;
+    const void* fn = smemw ? (const void*)prrlu_kernel<T, true> : (const void*)prrlu_kernel<T, false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&a};
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(PT), args, smem, st);
 }
 
 template cudaError_t launch_prrlu<double>(const PrrluArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_prrlu<cplx>(const PrrluArgs<cplx>&, int, cudaStream_t);
-template size_t prrlu_smem_bytes<double>(int, int, int);
-template size_t prrlu_smem_bytes<cplx>(int, int, int);
 
 }  // namespace aci
