@@ -68,6 +68,12 @@ aci_status aci_k_tt_random(aci_ctx *ctx, int32_t dtype, uint64_t seed, int32_t L
 aci_status aci_k_apply_pinv(aci_ctx *ctx, int32_t dtype, const void *T, int32_t R, int32_t k,
                             const void *LI, const void *D, const void *UJ, void *Y);
 
+/* The reciprocal 1/x the pivot search uses for its multipliers (Algorithm 2's Schur step
+ * divides by the pivot): an FP32 seed refined by two Newton-Raphson steps in FP64, within two
+ * units in the last place of 1/x for |x| in (1e-30, 1e30) and the correctly rounded 1/x outside.
+ * x and y are device arrays of n doubles. */
+aci_status aci_k_reciprocal(aci_ctx *ctx, const double *x, int32_t n, double *y);
+
 /* The pivot search of aci_k_prrlu for callers that cannot allocate device memory; the paper
  * has no counterpart (it concerns how this library obtains scratch memory, not the method).
  * Such callers include code inside a host application that owns all device memory and forbids

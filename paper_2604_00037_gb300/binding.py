@@ -58,7 +58,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 # Every symbol the headers declare; tests check the library exports each one.
 EXPORTS = ["aci_create", "aci_destroy", "aci_last_error", "aci_opts_default", "aci_elementwise",
            "aci_elementwise_ex", "aci_tt_release", "aci_k_frame_gemm", "aci_k_pi_block", "aci_k_prrlu",
-           "aci_k_tt_random", "aci_k_apply_pinv", "aci_k_prrlu_static"]
+           "aci_k_tt_random", "aci_k_apply_pinv", "aci_k_prrlu_static", "aci_k_reciprocal"]
 
 _lib = None
 
@@ -96,6 +96,7 @@ def load_library(build_if_missing: bool = True) -> C.CDLL:
                                 C.POINTER(i32), C.POINTER(dbl)]
     lib.aci_k_tt_random.argtypes = [vp, i32, C.c_uint64, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(vp)]
     lib.aci_k_apply_pinv.argtypes = [vp, i32, vp, i32, i32, vp, vp, vp, vp]
+    lib.aci_k_reciprocal.argtypes = [vp, vp, i32, vp]
     lib.aci_k_prrlu_static.argtypes = [vp, i32, vp, i32, i32, dbl, i32, vp, vp, vp, vp, vp,
                                        C.POINTER(i32), C.POINTER(dbl)]
     for name in EXPORTS:
@@ -342,6 +343,13 @@ class Context:
         self._check(self.lib.aci_k_tt_random(self.handle, ACI_C128 if complex_values else ACI_R64,
                                              int(seed), L, d, r, p))
         return cores
+
+    def reciprocal(self, x):
+        """1/x with the reciprocal of the pivot search (x: float64 CUDA tensor)."""
+        import torch
+        y = torch.empty_like(x)
+        self._check(self.lib.aci_k_reciprocal(self.handle, x.data_ptr(), x.numel(), y.data_ptr()))
+        return y
 
     def apply_pinv(self, T, LI, D, UJ):
         import torch

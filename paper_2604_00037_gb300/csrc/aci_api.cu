@@ -176,14 +176,17 @@ struct Run {
         pend.push_back({cls, a, b});
     }
     // After a stream sync: fold the finished event pairs into kms.
-    void harvest() {
+    // keep = true: the pairs belong to a captured graph and are read again after the next replay.
+    void harvest(bool keep = false) {
         for (auto& q : pend) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) kms[q.cls] += ms;
-            ctx->evfree.push_back(q.a);
-            ctx->evfree.push_back(q.b);
+            if (!keep) {
+                ctx->evfree.push_back(q.a);
+                ctx->evfree.push_back(q.b);
+            }
         }
-        pend.clear();
+        if (!keep) pend.clear();
     }
     double* flops_of(int cls) { return prof ? kflops + cls : nullptr; }
     double tol = 0;
@@ -591,11 +594,13 @@ struct Run {
             post(ACI_KCLASS_OTHER, e, "iter_snapshot");
         }
 
-        // ---- sweeps
-        int it = 0, converged = 0, fixed = 0;
-        aci::IterFlags fl;
-        std::memset(&fl, 0, sizeof(fl));
-        for (it = 1; it <= maxit; ++it) {
+        // ---- sweeps. One iteration (left-to-right and right-to-left sweeps, stop test, flag copy)
+        // is enqueued once into a CUDA graph and replayed: every shape is read on the device, so
+        // the launches are identical from one iteration to the next. It starts by clearing the
+        // pivot-search exchange area, so the tags of its launches are fresh at every replay.
+        auto enqueue_iteration = [&]() {
+            ck(ctx, cudaMemsetAsync(ll, 0, ll_words * sizeof(unsigned long long), st), "clear exchange");
+            prrlu_launches = 0;
             for (int b = 0; b < nb; ++b) {  // left to right, CI "right"
                 left_half(b);
                 pi_block(b);
@@ -612,15 +617,82 @@ struct Run {
             aci::launch_iter_check(L, chi, chi_prev, pcol_dev, jprev_dev, eps_lr, eps_rl, smax, err, flags, 0, st);
             post(ACI_KCLASS_OTHER, e, "iter_check");
             ck(ctx, cudaMemcpyAsync(ctx->hflags, flags, sizeof(aci::IterFlags), cudaMemcpyDeviceToHost, st), "flags");
+        };
+        struct GraphGuard {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t e = nullptr;
+            ~GraphGuard() {
+                if (e) cudaGraphExecDestroy(e);
+                if (g) cudaGraphDestroy(g);
+            }
+        } guard;
+        cudaGraph_t& graph = guard.g;
+        cudaGraphExec_t& gexec = guard.e;
+        long long per_iter_launches = 0;
+        long long per_iter_count[4] = {0, 0, 0, 0};
+        {
+            ck(ctx, cudaStreamSynchronize(st), "before capture");
+            harvest();
+            const long long l0 = ctx->launches;
+            long long c0[4];
+            for (int q = 0; q < 4; ++q) c0[q] = kcount[q];
+            // relaxed: the first use of a kernel may set its attributes or create events meanwhile
+            bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+            if (ok) {
+                try {
+                    enqueue_iteration();
+                } catch (Fail&) {
+                    ok = false;
+                }
+                cudaError_t e = cudaStreamEndCapture(st, &graph);
+                ok = ok && e == cudaSuccess && graph != nullptr;
+                if (ok) ok = cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess;
+            }
+            if (!ok) {  // enqueue directly instead
+                cudaGetLastError();
+                if (gexec) cudaGraphExecDestroy(gexec);
+                if (graph) cudaGraphDestroy(graph);
+                gexec = nullptr;
+                graph = nullptr;
+                for (auto& q : pend) {
+                    ctx->evfree.push_back(q.a);
+                    ctx->evfree.push_back(q.b);
+                }
+                pend.clear();
+                ctx->err.clear();
+            }
+            per_iter_launches = ctx->launches - l0;
+            for (int q = 0; q < 4; ++q) per_iter_count[q] = kcount[q] - c0[q];
+            ctx->launches = l0;
+            for (int q = 0; q < 4; ++q) kcount[q] = c0[q];
+        }
+        int it = 0, converged = 0, fixed = 0;
+        aci::IterFlags fl;
+        std::memset(&fl, 0, sizeof(fl));
+        for (it = 1; it <= maxit; ++it) {
+            if (gexec) {
+                ck(ctx, cudaGraphLaunch(gexec, st), "graph launch");
+                ctx->launches += per_iter_launches;
+                for (int q = 0; q < 4; ++q) kcount[q] += per_iter_count[q];
+            } else {
+                enqueue_iteration();
+            }
             ck(ctx, cudaStreamSynchronize(st), "sweep");
             fl = *ctx->hflags;
-            harvest();
+            harvest(gexec != nullptr);
             if (fl.err & aci::DEVERR_TIMEOUT) fail(ctx, ACI_E_TIMEOUT, "a device-side wait in the pivot search timed out");
             if ((fl.err & aci::DEVERR_NUMERIC) || !(fl.S < INFINITY))
                 fail(ctx, ACI_E_NUMERIC, "a non-finite value reached the pivot search");
             const double tau = rel ? tol * fl.S : tol;
             if (!fl.grew && fl.emax <= tau) { converged = 1; break; }
             if (fl.fixed) { fixed = 1; break; }
+        }
+        if (gexec) {
+            for (auto& q : pend) {
+                ctx->evfree.push_back(q.a);
+                ctx->evfree.push_back(q.b);
+            }
+            pend.clear();
         }
         if (it > maxit) it = maxit;
 
@@ -1089,6 +1161,21 @@ aci_status aci_k_tt_random(aci_ctx* ctx, int32_t dtype, uint64_t seed, int32_t L
         else fail(ctx, ACI_E_DTYPE, "unsupported dtype");
         note_launch(ctx, "tt_random");
         ck(ctx, cudaStreamSynchronize(ctx->stream), "tt_random");
+        return ACI_OK;
+    } catch (Fail& f) {
+        return f.st;
+    }
+}
+
+aci_status aci_k_reciprocal(aci_ctx* ctx, const double* x, int32_t n, double* y) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    try {
+        if (!x || !y || n < 1) fail(ctx, ACI_E_ARG, "bad arguments");
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        aci::launch_recip(x, n, y, ctx->stream);
+        note_launch(ctx, "reciprocal");
+        ck(ctx, cudaStreamSynchronize(ctx->stream), "reciprocal");
         return ACI_OK;
     } catch (Fail& f) {
         return f.st;

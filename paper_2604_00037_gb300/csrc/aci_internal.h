@@ -62,6 +62,8 @@ constexpr unsigned int kPrrluMaxLaunches = (1u << (32 - kPrrluStepBits)) - 1;
 template <class T> cudaError_t launch_prrlu(const PrrluArgs<T>& a, int G, cudaStream_t st);
 int prrlu_grid(int mmax, int nmax, int num_sms);
 size_t prrlu_ll_words(int mmax, int G, bool cplx_values);
+// y[i] = 1 / x[i] with the reciprocal the pivot search uses (step-level entry point).
+void launch_recip(const double* x, int n, double* y, cudaStream_t st);
 
 // Per-bond buffers used by the output assembly.
 template <class T> struct BondBuf {

@@ -25,6 +25,8 @@
 // The Schur update of step p is fused with the local argmax of step p+1.
 #include <climits>
 #include <cstdlib>
+#include <mutex>
+#include <set>
 
 #include <cooperative_groups.h>
 
@@ -109,9 +111,34 @@ __device__ __forceinline__ P* align16(void* p) {
 template <class T> struct __align__(16) Decision {
     int code;  // 0 = accept the pivot, 1 = stop, 2 = stop on a non-finite pivot
     int zpiv;  // the pivot is exactly zero (all-zero block)
+    int lin;   // winner's position and owning CTA (used by the register-resident kernel)
+    int gw;
     double eps;
     T inv;     // 1 / pivot (0 when zpiv)
+    T piv;
 };
+
+// 1/d for a real pivot: an FP32 reciprocal as the seed, then two Newton-Raphson steps
+// r <- r + r (1 - d r) in FP64 (each step squares the relative error: 2^-23 -> 2^-46 -> below
+// one ulp). On this GPU a dependent FP64 operation takes ~63 cycles and a correctly rounded
+// division ~570, and the reciprocal sits on the critical path of every pivot step. Outside the
+// FP32 exponent range the division is used instead.
+__device__ __forceinline__ double fast_recip(double d) {
+    // range test on the biased exponent (integer work): 2^-99 <= |d| < 2^100
+    const unsigned ex = ((unsigned)__double2hiint(d) >> 20) & 0x7FFu;
+    if (ex < 1023u - 99u || ex >= 1023u + 100u) return 1.0 / d;
+    double r = (double)(1.0f / (float)d);
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+__device__ __forceinline__ double recip_of(double d) { return fast_recip(d); }
+__device__ __forceinline__ cplx recip_of(cplx d) { return s_div(s_one(cplx()), d); }
+
+// The stop test of Algorithm 2 and the multiplier scale for the step's winner. For real values
+// |pivot| <= tau and pivot == 0 are decided on the key bits (exact: keys are non-negative
+// doubles), which keeps FP64 compares (~170 cycles each here) off the critical path.
 template <class T>
 __device__ __forceinline__ void decide(Decision<T>* d, kbits_t wkey, int wlin, T piv, int p, int kmax, double tau) {
     int code = 0;
@@ -122,16 +149,19 @@ __device__ __forceinline__ void decide(Decision<T>* d, kbits_t wkey, int wlin, T
         code = 1;
     } else {
         const double mag = key_to_mag(__longlong_as_double((long long)wkey), T());
+        const bool is_real = sizeof(T) == sizeof(double);
+        const bool below = is_real ? (wkey <= key_bits(tau)) : (mag <= tau);
+        const bool zero = is_real ? (wkey == 0) : s_iszero(piv);
         if (wkey >= key_bits(INFINITY)) {
             code = 2;
             e = mag;
-        } else if (p == kmax || (p >= 1 && mag <= tau)) {
+        } else if (p == kmax || (p >= 1 && below)) {
             code = 1;
             e = mag;
-        } else if (s_iszero(piv)) {
+        } else if (zero) {
             d->zpiv = 1;
         } else {
-            d->inv = s_div(s_one(T()), piv);
+            d->inv = recip_of(piv);
         }
     }
     d->code = code;
@@ -609,16 +639,28 @@ __device__ __forceinline__ cplx shfl_0(cplx v) {
     return mkc(__shfl_sync(0xffffffffu, v.re, 0), __shfl_sync(0xffffffffu, v.im, 0));
 }
 
+__device__ __forceinline__ double shfl_from(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ cplx shfl_from(cplx v, int src) {
+    return mkc(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
+}
+
+// Warp argmax of (key, lowest position) with single-instruction warp reductions: the max of the
+// high 32 key bits, then of the low 32 bits among those lanes, then the min position among the
+// lanes holding that key; the winner's value and tag travel by one shuffle. The result is the
+// same as a pairwise reduction with better(), in three reduction latencies instead of five
+// rounds of dependent shuffles.
 template <class T>
 __device__ __forceinline__ void warp_best(kbits_t& k, int& l, T& v, int& s) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const kbits_t ok = __shfl_xor_sync(0xffffffffu, k, off);
-        const int ol = __shfl_xor_sync(0xffffffffu, l, off);
-        const T ov = shfl_x(v, off);
-        const int os = __shfl_xor_sync(0xffffffffu, s, off);
-        if (better(ok, ol, k, l)) { k = ok; l = ol; v = ov; s = os; }
-    }
+    const unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
+    const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+    const bool top = hi == mhi && lo == mlo;
+    const unsigned ml = __reduce_min_sync(0xffffffffu, top ? (unsigned)l : 0xFFFFFFFFu);
+    const int src = __ffs(__ballot_sync(0xffffffffu, top && (unsigned)l == ml)) - 1;
+    k = ((kbits_t)mhi << 32) | mlo;
+    l = (int)ml;
+    v = shfl_from(v, src);
+    s = __shfl_sync(0xffffffffu, s, src);
 }
 
 template <class T, int ROWS, int WMAX>
@@ -639,6 +681,7 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
     T* prow = candcol + 2 * (size_t)mmax;
     Cand<T>* cand = align16<Cand<T>>(prow + WMAX);
     Cand<T>* wmx = cand + 2 * C;  // [RWARP]
+    Decision<T>* dec = reinterpret_cast<Decision<T>*>(wmx + RWARP);
 
     T v[ROWS][WMAX];
     bool live[ROWS];
@@ -706,34 +749,36 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
             for (int t = lane; t < C; t += 32) *cl.map_shared_rank(cand + par * C + g, t) = mine;
         }
         cl.sync();
-        // (2) the winner among the C candidates, and the step's decision (every warp)
-        kbits_t wk = 0;
-        int wl = INT_MAX, gw = 0;
-        T pv = s_zero(T());
-        for (int t = lane; t < C; t += 32) {
-            const Cand<T>& c = cand[par * C + t];
-            if (better(c.key, c.lin, wk, wl)) { wk = c.key; wl = c.lin; pv = c.val; gw = t; }
+        // (2) the winner among the C candidates and the step's decision: warp 0 only (the FP64
+        //     work of the decision is latency-bound), read by everyone after one barrier
+        if (warp == 0) {
+            kbits_t wk = 0;
+            int wl = INT_MAX, gw = 0;
+            T pv = s_zero(T());
+            for (int t = lane; t < C; t += 32) {
+                const Cand<T>& c = cand[par * C + t];
+                if (better(c.key, c.lin, wk, wl)) { wk = c.key; wl = c.lin; pv = c.val; gw = t; }
+            }
+            warp_best(wk, wl, pv, gw);
+            if (lane == 0) {
+                decide(dec, wk, wl, pv, p, kmax, tau);
+                dec->lin = wl;
+                dec->gw = gw;
+                dec->piv = pv;
+            }
         }
-        warp_best(wk, wl, pv, gw);
-        int code = 0, zpiv = 0;
-        double de = 0.0;
-        T inv = s_zero(T());
-        if (lane == 0) {
-            Decision<T> d;
-            decide(&d, wk, wl, pv, p, kmax, tau);
-            code = d.code;
-            zpiv = d.zpiv;
-            de = d.eps;
-            inv = d.inv;
-        }
-        code = __shfl_sync(0xffffffffu, code, 0);
+        __syncthreads();
+        const int code = dec->code;
         if (code) {
             if (code == 2 && g == 0 && tid == 0) atomicOr(a.err, DEVERR_NUMERIC);
-            eps = shfl_0(de);
+            eps = dec->eps;
             break;
         }
-        zpiv = __shfl_sync(0xffffffffu, zpiv, 0);
-        inv = shfl_0(inv);
+        const int zpiv = dec->zpiv;
+        const T inv = dec->inv;
+        const T pv = dec->piv;
+        const int gw = dec->gw;
+        const int wl = dec->lin;
         const int ri = wl / n, cj = wl % n;
         if (g == 0 && tid == 0) {
             a.piv_rows[p] = ri;
@@ -750,27 +795,27 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
             l[i] = s_zero(T());
             if (live[i] && r != ri && !zpiv) l[i] = s_mul(wcol[r], inv);
             if (a.L && r >= r0 && r < r1) a.L[(size_t)p * a.Lld + r] = (r == ri) ? s_one(T()) : l[i];
-            if (r == ri) {  // this thread holds the pivot row: publish it and row p of U
+            if (r == ri) {  // this thread holds the pivot row: publish it
 #pragma unroll
-                for (int cc = 0; cc < WMAX; ++cc) {
-                    prow[cc] = v[i][cc];
-                    if (a.U && cc < w) {
-                        T u;
-                        if (c0 + cc == cj) u = s_one(T());
-                        else if (!((colmask >> cc) & 1u) || zpiv) u = s_zero(T());
-                        else u = s_mul(v[i][cc], inv);
-                        a.U[(size_t)p * a.Uld + c0 + cc] = u;
-                    }
-                }
+                for (int cc = 0; cc < WMAX; ++cc) prow[cc] = v[i][cc];
                 live[i] = false;
             }
         }
+        const unsigned oldmask = colmask;
         if (cj >= c0 && cj < c1) colmask &= ~(1u << (cj - c0));
         __syncthreads();
+        if (a.U && tid < w) {  // row p of U for the own columns, one thread per column
+            const int c = c0 + tid;
+            T u;
+            if (c == cj) u = s_one(T());
+            else if (!((oldmask >> tid) & 1u) || zpiv) u = s_zero(T());
+            else u = s_mul(prow[tid], inv);
+            a.U[(size_t)p * a.Uld + c] = u;
+        }
         // (4) Schur-complement update in registers, fused with the next local argmax
-        bkey = 0;
-        blin = INT_MAX;
-        bval = s_zero(T());
+        kbits_t qk[4] = {0, 0, 0, 0};
+        int ql[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+        T qv[4] = {s_zero(T()), s_zero(T()), s_zero(T()), s_zero(T())};
 #pragma unroll
         for (int i = 0; i < ROWS; ++i) {
             if (!live[i]) continue;
@@ -781,10 +826,16 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
                     const T x = s_fms(l[i], prow[cc], v[i][cc]);
                     v[i][cc] = x;
                     const kbits_t k = key_of(x);
-                    if (better(k, rn + cc, bkey, blin)) { bkey = k; blin = rn + cc; bval = x; }
+                    if (better(k, rn + cc, qk[cc & 3], ql[cc & 3])) { qk[cc & 3] = k; ql[cc & 3] = rn + cc; qv[cc & 3] = x; }
                 }
             }
         }
+        bkey = qk[0];
+        blin = ql[0];
+        bval = qv[0];
+#pragma unroll
+        for (int q = 1; q < 4; ++q)
+            if (better(qk[q], ql[q], bkey, blin)) { bkey = qk[q]; blin = ql[q]; bval = qv[q]; }
         ++p;
     }
     if (g == 0 && tid == 0) {
@@ -805,7 +856,7 @@ template <class T>
 size_t creg_bytes(int mmax, int C, int wmax) {
     size_t b = sizeof(T) * (2 * (size_t)mmax + wmax);
     b = (b + 15) & ~(size_t)15;
-    b += sizeof(Cand<T>) * (2 * (size_t)C + RWARP);
+    b += sizeof(Cand<T>) * (2 * (size_t)C + RWARP) + sizeof(Decision<T>);
     return b;
 }
 
@@ -879,6 +930,21 @@ int max_cluster() {
     return v;
 }
 
+// Shared-memory and cluster-size attributes of a kernel, set once per kernel (host calls such as
+// these cost microseconds and would otherwise sit between short launches).
+cudaError_t kernel_attrs(const void* fn) {
+    static std::mutex mu;
+    static std::set<const void*> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count(fn)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) cudaGetLastError();  // kernels launched without clusters do not need it
+    done.insert(fn);
+    return cudaSuccess;
+}
+
 // Blocks whose FP64 update work (entries, x4 for complex) is at most this run in one cluster.
 constexpr long long kClusterWorkMax = 1LL << 18;
 
@@ -924,8 +990,7 @@ cudaError_t launch_prrlu(const PrrluArgs<T>& a_in, int G, cudaStream_t st) {
             a.wcap_cols = wmax;
             a.wcap_elems = 0;
             const size_t smem = creg_bytes<T>(a.mmax, C, wmax);
-            cudaError_t e = cudaFuncSetAttribute(reg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
-            if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute(reg, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaError_t e = kernel_attrs((const void*)reg);
             if (e != cudaSuccess) return e;
             cfg.blockDim = dim3(RT);
             cfg.dynamicSmemBytes = smem;
@@ -938,8 +1003,7 @@ cudaError_t launch_prrlu(const PrrluArgs<T>& a_in, int G, cudaStream_t st) {
         const size_t smem = cluster_bytes<T>(a.mmax, C, a.wcap_elems, a.wcap_cols, smemw);
         if (smem > kSmemLimit) return cudaErrorInvalidValue;
         void (*fn)(PrrluArgs<T>) = smemw ? prrlu_cluster_kernel<T, true> : prrlu_cluster_kernel<T, false>;
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
-        if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaError_t e = kernel_attrs((const void*)fn);
         if (e != cudaSuccess) return e;
         cfg.blockDim = dim3(PT);
         cfg.dynamicSmemBytes = smem;
@@ -953,11 +1017,32 @@ cudaError_t launch_prrlu(const PrrluArgs<T>& a_in, int G, cudaStream_t st) {
     const bool smemw = layout_bytes<T>(a.mmax, G, a.wcap_elems, a.wcap_cols, true) <= kSmemLimit;
     const size_t smem = layout_bytes<T>(a.mmax, G, a.wcap_elems, a.wcap_cols, smemw);
     if (smem > kSmemLimit) return cudaErrorInvalidValue;
-    const void* fn = smemw ? (const void*)prrlu_kernel<T, true> : (const void*)prrlu_kernel<T, false>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+    void (*fn)(PrrluArgs<T>) = smemw ? prrlu_kernel<T, true> : prrlu_kernel<T, false>;
+    cudaError_t e = kernel_attrs((const void*)fn);
     if (e != cudaSuccess) return e;
-    void* args[] = {&a};
-    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(PT), args, smem, st);
+    // a cooperative launch (all CTAs co-resident), expressed so that stream capture accepts it
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(PT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, a);
+}
+
+namespace {
+__global__ void recip_kernel(const double* x, int n, double* y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = recip_of(x[i]);
+}
+}  // namespace
+
+void launch_recip(const double* x, int n, double* y, cudaStream_t st) {
+    if (n > 0) recip_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, n, y);
 }
 
 template cudaError_t launch_prrlu<double>(const PrrluArgs<double>&, int, cudaStream_t);

@@ -150,3 +150,14 @@ def test_apply_pinv(ctx, cplx):
     P = LI @ np.diag(f["D"]) @ UJ
     ref = np.linalg.solve(P.T, T.T).T
     assert rel(got, ref) <= 1e-10
+
+
+def test_pivot_reciprocal_within_two_ulp(ctx):
+    """The pivot search's reciprocal (FP32 seed + two Newton-Raphson steps) against 1/x."""
+    rng = np.random.default_rng(17)
+    x = np.concatenate([rng.uniform(-1, 1, 4000) * 10.0 ** rng.uniform(-29, 29, 4000),
+                        [1.0, -3.0, 0.1, 1e-200, -1e250, 1e-300]])
+    y = ctx.reciprocal(dev(x)).cpu().numpy()
+    ref = 1.0 / x
+    ulp = np.spacing(np.abs(ref))
+    assert (np.abs(y - ref) <= 2 * ulp).all()
