@@ -212,6 +212,9 @@ struct Run {
     aci::IterFlags* flags = nullptr;
     T* ones = nullptr;
     T* W = nullptr;
+    T* gpart = nullptr;                 // GEMM partial tiles
+    int* gcount = nullptr;              // GEMM per-tile counters (kept zeroed)
+    size_t gpart_elems = 1, gcount_n = 1;
     unsigned long long* ll = nullptr;  // pivot-search exchange words
     size_t ll_words = 0;
     unsigned int prrlu_launches = 0;   // launches since the exchange area was last cleared
@@ -290,6 +293,8 @@ struct Run {
         ones = c.take<T>(1);
         W = c.take<T>(wcap);
         ll = c.take<unsigned long long>(ll_words);
+        gpart = c.take<T>(gpart_elems);
+        gcount = c.take<int>(gcount_n);
         bonds_dev = c.take<aci::BondBuf<T>>(std::max(nb, 1));
         Yptr_dev = c.take<T*>(L);
         pcol_dev = c.take<int*>(std::max(nb, 1));
@@ -335,6 +340,21 @@ struct Run {
             if ((long long)mcap[b] * ncap[b] >= (1LL << 31))
                 fail(ctx, ACI_E_SHAPE, "a Pi block would exceed 2^31 entries");
         }
+        auto need = [&](int Mm, int Nm, int nprod, int combine) {
+            gpart_elems = std::max(gpart_elems, aci::gemm_part_elems(Mm, Nm, nprod, combine, ctx->num_sms));
+            gcount_n = std::max(gcount_n, aci::gemm_tile_counters(Mm, Nm, nprod));
+        };
+        int rmax = 1;
+        for (int n = 0; n < N; ++n)
+            for (int s = 0; s <= L; ++s) rmax = std::max(rmax, r[n][s]);
+        const int dmax = *std::max_element(d.begin(), d.end());
+        for (int b = 0; b < nb; ++b) need(mcap[b], ncap[b], N, 1);
+        for (int s = 0; s < L; ++s) {
+            need(cap[s], dmax * rmax, N, 0);           // left half-products
+            need(rmax * dmax, cap[s + 1], N, 0);       // right half-products
+            need(ry[s] * d[s], cap[s + 1], 1, 0);      // initial CI
+        }
+        need(dmax, 1, N, 1);                           // single site
         for (int s = 1; s < L; ++s) {
             const int m = ry[s], n = d[s] * cap[s + 1];
             wcap = std::max(wcap, (size_t)m * n);
@@ -349,6 +369,10 @@ struct Run {
     void gemm(aci::GemmArgs<T>& g, int Mmax, int Nmax, const char* what, int cls) {
         g.chi = chi;
         g.flops = flops_of(cls);
+        g.part = gpart;
+        g.tile_count = gcount;
+        g.target_units = aci::gemm_target_units(ctx->num_sms);
+        g.num_sms = ctx->num_sms;
         cudaEvent_t e = pre(cls);
         aci::launch_gemm<T>(g, Mmax, Nmax, st);
         post(cls, e, what);
@@ -495,6 +519,7 @@ struct Run {
         ck(ctx, cudaMemsetAsync(kflops, 0, 4 * sizeof(double), st), "memset");
         ck(ctx, cudaMemsetAsync(ll, 0, ll_words * sizeof(unsigned long long), st), "clear exchange");
         prrlu_launches = 0;
+        ck(ctx, cudaMemsetAsync(gcount, 0, gcount_n * sizeof(int), st), "clear counters");
         T one_h;
         std::memset(&one_h, 0, sizeof(T));
         *reinterpret_cast<double*>(&one_h) = 1.0;
@@ -981,11 +1006,21 @@ aci_status aci_k_frame_gemm(aci_ctx* ctx, int32_t dtype, const void* A, const in
     try {
         if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < 1) fail(ctx, ACI_E_ARG, "bad arguments");
         ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
-        int* dummy = reinterpret_cast<int*>(workspace(ctx, 256));
         auto go = [&](auto tag) {
             using T = decltype(tag);
+            const size_t np = aci::gemm_part_elems(M, N, 1, 0, ctx->num_sms);
+            const size_t nc = aci::gemm_tile_counters(M, N, 1);
+            char* ws = workspace(ctx, 512 + np * sizeof(T) + nc * sizeof(int));
+            int* dummy = reinterpret_cast<int*>(ws);
+            T* part = reinterpret_cast<T*>(ws + 256);
+            int* cnt = reinterpret_cast<int*>(ws + 256 + np * sizeof(T));
+            ck(ctx, cudaMemsetAsync(cnt, 0, nc * sizeof(int), ctx->stream), "memset");
             aci::GemmArgs<T> g;
             std::memset(&g, 0, sizeof(g));
+            g.part = part;
+            g.tile_count = cnt;
+            g.target_units = aci::gemm_target_units(ctx->num_sms);
+            g.num_sms = ctx->num_sms;
             g.A[0] = static_cast<const T*>(A);
             g.B[0] = static_cast<const T*>(B);
             g.C[0] = static_cast<T*>(C);
@@ -1019,14 +1054,23 @@ aci_status aci_k_pi_block(aci_ctx* ctx, int32_t dtype, int32_t nprod, const void
         if (!A || !B || !K || !Pi || M < 1 || N < 1 || nprod < 1 || nprod > 2) fail(ctx, ACI_E_ARG, "bad arguments");
         if (op.kind < ACI_OP_MUL || op.kind > ACI_OP_AFFINE) fail(ctx, ACI_E_ARG, "unknown op kind");
         ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
-        char* ws = workspace(ctx, 512);
+        const size_t np = aci::gemm_part_elems(M, N, nprod, 1, ctx->num_sms);
+        const size_t nc = aci::gemm_tile_counters(M, N, nprod);
+        char* ws = workspace(ctx, 1024 + np * sizeof(cplx) + nc * sizeof(int));
         int* dummy = reinterpret_cast<int*>(ws);
         unsigned long long* smax = reinterpret_cast<unsigned long long*>(ws + 256);
+        int* cnt = reinterpret_cast<int*>(ws + 512);
+        void* part_raw = ws + 512 + ((nc * sizeof(int) + 255) & ~(size_t)255);
         ck(ctx, cudaMemsetAsync(smax, 0, 8, ctx->stream), "memset");
+        ck(ctx, cudaMemsetAsync(cnt, 0, nc * sizeof(int), ctx->stream), "memset");
         auto go = [&](auto tag) {
             using T = decltype(tag);
             aci::GemmArgs<T> g;
             std::memset(&g, 0, sizeof(g));
+            g.part = static_cast<T*>(part_raw);
+            g.tile_count = cnt;
+            g.target_units = aci::gemm_target_units(ctx->num_sms);
+            g.num_sms = ctx->num_sms;
             for (int n = 0; n < nprod; ++n) {
                 if (K[n] < 1) fail(ctx, ACI_E_ARG, "K must be >= 1");
                 g.A[n] = static_cast<const T*>(A[n]);

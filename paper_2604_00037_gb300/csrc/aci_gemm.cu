@@ -5,11 +5,16 @@
 //  * the Pi block (Eq. (pifromframes)) with f applied in the epilogue (Eq. (localupdate)):
 //      Pi = f(LX^1 XR^1, ..., LX^N XR^N), written once, with max|Pi| folded into a running maximum.
 // Shapes that depend on ranks chosen on the device are read from the device rank array, so a
-// whole sweep can be enqueued without host round trips; CTAs outside the live shape exit.
+// whole sweep can be enqueued without host round trips.
 //
-// GB300 runs FP64 at about 2 FMA/clk/SM (measured 1.2 TFLOP/s for the whole GPU), so these
-// kernels are bound by the FP64 pipe, not by memory: what matters is that every SM gets work.
-// The tile is 32 x 32 with 256 threads (2 x 2 outputs each, per product).
+// GB300 design. FP64 runs at 2 multiply-adds per clock per SM (1.2 TFLOP/s for the GPU, with
+// ~63-cycle latency), so one CTA computing a 32 x 32 tile over K = 256 needs ~60 us: what matters
+// is that every SM gets a share of every contraction, including the many small ones of a sweep.
+// The live shape is cut into units (32 x 32 output tile, K chunk, product), with enough K chunks
+// that the units outnumber the SMs about four to one; a fixed grid of CTAs strides over them and
+// writes each unit's partial tile to scratch. The last CTA to finish a tile (a per-tile counter,
+// reset by that CTA) sums the tile's partials in a fixed order, applies f and folds the running
+// maximum, so the result does not depend on the order in which CTAs finish.
 #include "aci_internal.h"
 
 namespace aci {
@@ -18,56 +23,118 @@ namespace {
 
 constexpr int BM = 32, BN = 32, BK = 16, NT = 256;
 constexpr int TM = 2, TN = 2;  // per-thread outputs; 16 x 16 threads
+constexpr int kMinKChunk = 8;
 
 template <class T>
 __device__ __forceinline__ T ld_or_zero(const T* p, bool ok) {
     return ok ? *p : s_zero(T());
+}
+// Loads of other CTAs' partial tiles go through L2.
+__device__ __forceinline__ double ldcg_t(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ cplx ldcg_t(const cplx* p) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+    return mkc(v.x, v.y);
+}
+
+struct Plan {
+    int M[2], N[2], K[2];
+    int tiles[2];  // output tiles per product (combine: one shared output)
+    int kc;        // K chunks per product
+    int units;
+    int nout;      // outputs (combine: 1)
+};
+
+template <class T>
+__device__ __forceinline__ Plan make_plan(const GemmArgs<T>& g) {
+    Plan pl;
+    const int nq = g.nprod;
+    int maxkc = 1, tiles_total = 0;
+    for (int q = 0; q < 2; ++q) {
+        pl.M[q] = pl.N[q] = pl.K[q] = 0;
+        pl.tiles[q] = 0;
+    }
+    pl.nout = g.combine ? 1 : nq;
+    for (int q = 0; q < nq; ++q) {
+        const int z = g.combine ? 0 : q;
+        pl.M[q] = dimv(g.M[z], g.chi);
+        pl.N[q] = dimv(g.N[z], g.chi);
+        pl.K[q] = dimv(g.K[q], g.chi);
+        const int kc = (pl.K[q] + kMinKChunk - 1) / kMinKChunk;
+        maxkc = kc > maxkc ? kc : maxkc;
+    }
+    for (int o = 0; o < pl.nout; ++o) {
+        pl.tiles[o] = ((pl.M[o] + BM - 1) / BM) * ((pl.N[o] + BN - 1) / BN);
+        tiles_total += pl.tiles[o];
+    }
+    const int per_kc = g.combine ? tiles_total * nq : tiles_total;
+    int kc = (g.target_units + per_kc - 1) / (per_kc > 0 ? per_kc : 1);
+    kc = kc < 1 ? 1 : (kc > maxkc ? maxkc : kc);
+    pl.kc = kc;
+    pl.units = per_kc * kc;
+    return pl;
 }
 
 template <class T>
 __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];
-    const int* chi = g.chi;
-    const int z = g.combine ? 0 : blockIdx.z;
-    const int M = dimv(g.M[z], chi);
-    const int N = dimv(g.N[z], chi);
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    if (m0 >= M || n0 >= N) return;
+    __shared__ int s_last;
+    const Plan pl = make_plan(g);
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
-    const int nprod = g.combine ? g.nprod : 1;
+    const int nq = g.nprod;
 
-    T acc[2][TM][TN];
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
+    if (g.flops && blockIdx.x == 0 && tid == 0) {
+        const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
+        double f = 0.0;
+        for (int q = 0; q < nq; ++q) f += per * (double)pl.M[q] * (double)pl.N[q] * (double)pl.K[q];
+        atomicAdd(g.flops, f);
+    }
+
+    for (int u = blockIdx.x; u < pl.units; u += gridDim.x) {
+        // decode the unit: (output o, tile t, product q, K chunk c)
+        int o, t, q, c;
+        if (g.combine) {
+            o = 0;
+            t = u % pl.tiles[0];
+            const int rest = u / pl.tiles[0];
+            c = rest % pl.kc;
+            q = rest / pl.kc;
+        } else {
+            const int per0 = pl.tiles[0] * pl.kc;
+            o = (u < per0) ? 0 : 1;
+            const int uu = o == 0 ? u : u - per0;
+            t = uu % pl.tiles[o];
+            c = uu / pl.tiles[o];
+            q = o;
+        }
+        const int M = pl.M[o], N = pl.N[o], K = pl.K[q];
+        const int tcols = (N + BN - 1) / BN;
+        const int m0 = (t / tcols) * BM, n0 = (t % tcols) * BN;
+        const int ka = (int)(((long long)K * c) / pl.kc), kb = (int)(((long long)K * (c + 1)) / pl.kc);
+        const T* A = g.A[q];
+        const T* B = g.B[q];
+        const int lda = dimv(g.lda[q], g.chi);
+        const int ldb = dimv(g.ldb[q], g.chi);
+
+        T acc[TM][TN];
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
-            for (int j = 0; j < TN; ++j) acc[q][i][j] = s_zero(T());
-
-    for (int q = 0; q < nprod; ++q) {
-        const int pz = g.combine ? q : z;
-        const T* A = g.A[pz];
-        const T* B = g.B[pz];
-        const int K = dimv(g.K[pz], chi);
-        const int lda = dimv(g.lda[pz], chi);
-        const int ldb = dimv(g.ldb[pz], chi);
-        for (int k0 = 0; k0 < K; k0 += BK) {
-            // A tile: BM rows x BK columns, rows optionally gathered.
+            for (int j = 0; j < TN; ++j) acc[i][j] = s_zero(T());
+        for (int k0 = ka; k0 < kb; k0 += BK) {
             for (int e = tid; e < BM * BK; e += NT) {
                 const int i = e / BK, kk = e % BK;
                 const int gr = m0 + i, gk = k0 + kk;
-                const bool ok = gr < M && gk < K;
+                const bool ok = gr < M && gk < kb;
                 int src = 0;
                 if (ok) src = g.arow ? g.arow[gr] : gr;
                 As[kk][i] = ld_or_zero(A + (size_t)src * lda + gk, ok);
             }
-            // B tile: BK rows x BN columns, columns optionally gathered.
             for (int e = tid; e < BK * BN; e += NT) {
                 const int kk = e / BN, j = e % BN;
                 const int gk = k0 + kk, gc = n0 + j;
-                const bool ok = gk < K && gc < N;
+                const bool ok = gk < kb && gc < N;
                 int col = 0;
                 if (ok) col = g.bcol ? g.bcol[gc] : gc;
                 Bs[kk][j] = ld_or_zero(B + (size_t)gk * ldb + col, ok);
@@ -83,60 +150,92 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
 #pragma unroll
                 for (int i = 0; i < TM; ++i)
 #pragma unroll
-                    for (int j = 0; j < TN; ++j) acc[q][i][j] = s_fma(a[i], b[j], acc[q][i][j]);
+                    for (int j = 0; j < TN; ++j) acc[i][j] = s_fma(a[i], b[j], acc[i][j]);
             }
             __syncthreads();
         }
-    }
-
-    if (g.flops && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
-        const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
-        double f = 0.0;
-        for (int q = 0; q < nprod; ++q) {
-            const int pz = g.combine ? q : z;
-            f += per * (double)M * (double)N * (double)dimv(g.K[pz], chi);
-        }
-        atomicAdd(g.flops, f);
-    }
-
-    // Epilogue: f over the products (combine) or a plain store (batch); running max |C|,
-    // taken on key bits (integer max) and turned into a magnitude once per warp.
-    unsigned long long mk = 0;
-    T* C = g.C[z];
+        // partial tile -> scratch slot (q, c, t) of output o
+        const int tile_id = (o == 0 ? 0 : pl.tiles[0]) + t;
+        const int slot = (g.combine ? (q * pl.kc + c) * pl.tiles[0] + t : (o == 0 ? c * pl.tiles[0] + t
+                                                                              : pl.tiles[0] * pl.kc + c * pl.tiles[1] + t));
+        T* part = g.part + (size_t)slot * (BM * BN);
 #pragma unroll
-    for (int i = 0; i < TM; ++i) {
-        const int gr = m0 + ty * TM + i;
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) {
-            const int gc = n0 + tx * TN + j;
-            if (gr < M && gc < N) {
-                T v = g.combine ? apply_f(g.op, acc[0][i][j], acc[1][i][j]) : acc[0][i][j];
-                C[(size_t)gr * N + gc] = v;
-                const unsigned long long k = key_of(v);
-                mk = k > mk ? k : mk;  // NaN bits sort above +inf
+            for (int j = 0; j < TN; ++j) part[(ty * TM + i) * BN + tx * TN + j] = acc[i][j];
+        __threadfence();
+        __syncthreads();
+        const int expected = g.combine ? pl.kc * nq : pl.kc;
+        if (tid == 0) s_last = (atomicAdd(g.tile_count + tile_id, 1) == expected - 1);
+        __syncthreads();
+        if (!s_last) continue;
+        __threadfence();
+        // the last CTA of this tile: fixed-order sum of the partials, f, store, running max
+        unsigned long long mk = 0;
+        T* C = g.C[o];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int lr = ty * TM + i, gr = m0 + lr;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int lc = tx * TN + j, gc = n0 + lc;
+                T v;
+                if (g.combine) {
+                    T s[2] = {s_zero(T()), s_zero(T())};
+                    for (int qq = 0; qq < nq; ++qq)
+                        for (int cc = 0; cc < pl.kc; ++cc)
+                            s[qq] = s_add(s[qq], ldcg_t(g.part + (size_t)((qq * pl.kc + cc) * pl.tiles[0] + t) * (BM * BN) +
+                                                             lr * BN + lc));
+                    v = apply_f(g.op, s[0], s[1]);
+                } else {
+                    v = s_zero(T());
+                    for (int cc = 0; cc < pl.kc; ++cc) {
+                        const int sl = (o == 0) ? cc * pl.tiles[0] + t : pl.tiles[0] * pl.kc + cc * pl.tiles[1] + t;
+                        v = s_add(v, ldcg_t(g.part + (size_t)sl * (BM * BN) + lr * BN + lc));
+                    }
+                }
+                if (gr < M && gc < N) {
+                    C[(size_t)gr * N + gc] = v;
+                    const unsigned long long k = key_of(v);
+                    mk = k > mk ? k : mk;  // NaN bits sort above +inf
+                }
             }
         }
-    }
-    if (g.smax) {
+        if (tid == 0) g.tile_count[tile_id] = 0;  // ready for the next launch
+        if (g.smax) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, mk, off);
-            mk = o > mk ? o : mk;
-        }
-        // |v| = key for real, sqrt(key) for complex; sqrt is monotone, so the max commutes with it.
-        if ((tid & 31) == 0) {
-            const double mag = key_to_mag(__longlong_as_double((long long)mk), T());
-            atomicMax(g.smax, (unsigned long long)__double_as_longlong(mag));
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long ov = __shfl_xor_sync(0xffffffffu, mk, off);
+                mk = ov > mk ? ov : mk;
+            }
+            // |v| = key for real, sqrt(key) for complex; sqrt is monotone, so the max commutes with it.
+            if ((tid & 31) == 0) {
+                const double mag = key_to_mag(__longlong_as_double((long long)mk), T());
+                atomicMax(g.smax, (unsigned long long)__double_as_longlong(mag));
+            }
         }
     }
 }
 
 }  // namespace
 
+int gemm_target_units(int num_sms) { return 4 * num_sms; }
+
+size_t gemm_part_elems(int Mmax, int Nmax, int nprod, int combine, int num_sms) {
+    const size_t tiles = (size_t)((Mmax + BM - 1) / BM) * ((Nmax + BN - 1) / BN);
+    const size_t per_kc = combine ? tiles * nprod : tiles * nprod;
+    // units < target + per_kc (k chunks are rounded up from target / per_kc)
+    return (size_t)(gemm_target_units(num_sms) + per_kc) * BM * BN;
+}
+
+size_t gemm_tile_counters(int Mmax, int Nmax, int nprod) {
+    return (size_t)((Mmax + BM - 1) / BM) * ((Nmax + BN - 1) / BN) * nprod;
+}
+
 template <class T>
 void launch_gemm(const GemmArgs<T>& g, int Mmax, int Nmax, cudaStream_t st) {
     if (Mmax <= 0 || Nmax <= 0) return;
-    dim3 grid((Nmax + BN - 1) / BN, (Mmax + BM - 1) / BM, g.combine ? 1 : g.nprod);
+    const int grid = 2 * g.num_sms;
     gemm_kernel<T><<<grid, NT, 0, st>>>(g);
 }
 

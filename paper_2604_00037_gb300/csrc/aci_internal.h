@@ -21,9 +21,16 @@ template <class T> struct GemmArgs {
     OpParams<T> op;
     unsigned long long* smax;  // optional running max |C| (bits of a non-negative double)
     double* flops;             // optional: algorithmic flops of the launch are added here
+    T* part;                   // scratch for partial tiles: gemm_part_elems(...) elements
+    int* tile_count;           // zeroed counters: gemm_tile_counters(...) of them (left zeroed)
+    int target_units;          // gemm_target_units(num_sms)
+    int num_sms;
 };
 
 template <class T> void launch_gemm(const GemmArgs<T>& g, int Mmax, int Nmax, cudaStream_t st);
+int gemm_target_units(int num_sms);
+size_t gemm_part_elems(int Mmax, int Nmax, int nprod, int combine, int num_sms);
+size_t gemm_tile_counters(int Mmax, int Nmax, int nprod);
 
 template <class T> struct PrrluArgs {
     const T* Min;       // m x n row-major input, not modified
