@@ -140,7 +140,8 @@ __device__ __forceinline__ cplx recip_of(cplx d) { return s_div(s_one(cplx()), d
 // |pivot| <= tau and pivot == 0 are decided on the key bits (exact: keys are non-negative
 // doubles), which keeps FP64 compares (~170 cycles each here) off the critical path.
 template <class T>
-__device__ __forceinline__ void decide(Decision<T>* d, kbits_t wkey, int wlin, T piv, int p, int kmax, double tau) {
+__device__ __forceinline__ void decide(Decision<T>* d, kbits_t wkey, int wlin, T piv, int p, int kmax, double tau,
+                                       bool with_inv = true) {
     int code = 0;
     double e = 0.0;
     d->zpiv = 0;
@@ -160,7 +161,7 @@ __device__ __forceinline__ void decide(Decision<T>* d, kbits_t wkey, int wlin, T
             e = mag;
         } else if (zero) {
             d->zpiv = 1;
-        } else {
+        } else if (with_inv) {
             d->inv = recip_of(piv);
         }
     }
@@ -761,7 +762,7 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
             }
             warp_best(wk, wl, pv, gw);
             if (lane == 0) {
-                decide(dec, wk, wl, pv, p, kmax, tau);
+                decide(dec, wk, wl, pv, p, kmax, tau, false);
                 dec->lin = wl;
                 dec->gw = gw;
                 dec->piv = pv;
@@ -775,7 +776,6 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
             break;
         }
         const int zpiv = dec->zpiv;
-        const T inv = dec->inv;
         const T pv = dec->piv;
         const int gw = dec->gw;
         const int wl = dec->lin;
@@ -785,25 +785,34 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
             a.piv_cols[p] = cj;
             a.D[p] = pv;
         }
-        // (3) multipliers of the own rows, from the owner's candidate column
+        // (3) reads of the winning column from its owner's shared memory start here; thread 0
+        //     forms the pivot reciprocal while they are in flight, and it is read after the
+        //     barrier that also publishes the pivot row.
         const T* wcol = cl.map_shared_rank(candcol + (size_t)par * mmax, gw);
-        T l[ROWS];
-        const int r0 = (int)(((long long)m * g) / C), r1 = (int)(((long long)m * (g + 1)) / C);
+        T wv[ROWS];
 #pragma unroll
         for (int i = 0; i < ROWS; ++i) {
             const int r = tid + i * RT;
-            l[i] = s_zero(T());
-            if (live[i] && r != ri && !zpiv) l[i] = s_mul(wcol[r], inv);
-            if (a.L && r >= r0 && r < r1) a.L[(size_t)p * a.Lld + r] = (r == ri) ? s_one(T()) : l[i];
+            wv[i] = (live[i] && r != ri && !zpiv) ? wcol[r] : s_zero(T());
             if (r == ri) {  // this thread holds the pivot row: publish it
 #pragma unroll
                 for (int cc = 0; cc < WMAX; ++cc) prow[cc] = v[i][cc];
                 live[i] = false;
             }
         }
+        if (tid == 0 && !zpiv) dec->inv = recip_of(pv);
         const unsigned oldmask = colmask;
         if (cj >= c0 && cj < c1) colmask &= ~(1u << (cj - c0));
         __syncthreads();
+        const T inv = zpiv ? s_zero(T()) : dec->inv;
+        T l[ROWS];
+        const int r0 = (int)(((long long)m * g) / C), r1 = (int)(((long long)m * (g + 1)) / C);
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+            const int r = tid + i * RT;
+            l[i] = s_mul(wv[i], inv);
+            if (a.L && r >= r0 && r < r1) a.L[(size_t)p * a.Lld + r] = (r == ri) ? s_one(T()) : l[i];
+        }
         if (a.U && tid < w) {  // row p of U for the own columns, one thread per column
             const int c = c0 + tid;
             T u;
