@@ -56,7 +56,26 @@ typedef struct {
 
 typedef enum { ACI_TOL_REL = 0, ACI_TOL_ABS = 1 } aci_tol_kind;
 typedef enum { ACI_PIVOT_FULL = 0 } aci_pivot_mode;   /* full search of Algorithm 2 */
-typedef enum { ACI_PREC_FP64 = 0 } aci_precision;     /* every step in FP64 / complex128 */
+/* Arithmetic of the contractions (the frame half-products of Algorithm 5 and the Pi blocks of
+ * Eq. (pifromframes)). The pivot search (Algorithm 2), its Schur updates and error estimates and
+ * the output assembly Y = T P^-1 run in FP64 / complex128 in every mode.
+ *  ACI_PREC_FP64       FP64 / complex128 multiply-adds (default).
+ *  ACI_PREC_BF16X2..8  s = 2..8 exact BF16 digit planes per operand on the tensor cores: row r of
+ *                      A and column c of B are scaled by powers of two 2^e_r > max|A[r,:]|,
+ *                      2^f_c > max|B[:,c]| and truncated to s signed digits of b <= 7 bits
+ *                      (b the largest with s K (2^b - 1)^2 < 2^24, K doubled for complex); digit
+ *                      products of order i + j < s are summed exactly in FP32 and recombined in
+ *                      FP64. Per entry |err| <= K 2^(e_r + f_c) 2^(-b s) (s + 3.1). */
+typedef enum {
+    ACI_PREC_FP64 = 0,
+    ACI_PREC_BF16X2 = 2,
+    ACI_PREC_BF16X3 = 3,
+    ACI_PREC_BF16X4 = 4,
+    ACI_PREC_BF16X5 = 5,
+    ACI_PREC_BF16X6 = 6,
+    ACI_PREC_BF16X7 = 7,
+    ACI_PREC_BF16X8 = 8
+} aci_precision;
 
 /* A tensor train. For inputs every field is set by the caller. For outputs the library
  * fills it: d, rank and core are library-owned until aci_tt_release(). */
@@ -112,6 +131,8 @@ typedef struct {
     double kernel_ms[4];   /* profile = 1: summed device time per aci_kernel_class              */
     int64_t kernel_count[4];   /* launches per class (always filled)                           */
     double kernel_flops[4];    /* profile = 1: algorithmic flops per class                      */
+    double tensor_flops[4];    /* profile = 1: BF16 tensor-core flops issued per class (digit-plane
+                                  precisions; 0 for ACI_PREC_FP64)                               */
 } aci_stats;
 
 /* Device memory hooks. alloc returns a device pointer of at least `bytes` bytes aligned to

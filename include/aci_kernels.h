@@ -36,6 +36,18 @@ aci_status aci_k_pi_block(aci_ctx *ctx, int32_t dtype, int32_t nprod, const void
                           const void *const *B, int32_t M, int32_t N, const int32_t *K,
                           aci_op op, void *Pi, double *maxabs);
 
+/* aci_k_frame_gemm and aci_k_pi_block in the arithmetic `precision` selects (aci_precision):
+ * ACI_PREC_FP64 runs the FP64 kernels of the two calls above; ACI_PREC_BF16X2..8 runs the
+ * tensor-core digit-plane contraction aci_elementwise_ex uses at that precision (error bound in
+ * aci.h). Other values give ACI_E_ARG. Arguments and results are otherwise those of the two calls. */
+aci_status aci_k_frame_gemm_prec(aci_ctx *ctx, int32_t dtype, int32_t precision, const void *A,
+                                 const int32_t *arows, int32_t M, int32_t K, int32_t lda,
+                                 const void *B, const int32_t *bcols, int32_t N, int32_t ldb,
+                                 void *C);
+aci_status aci_k_pi_block_prec(aci_ctx *ctx, int32_t dtype, int32_t precision, int32_t nprod,
+                               const void *const *A, const void *const *B, int32_t M, int32_t N,
+                               const int32_t *K, aci_op op, void *Pi, double *maxabs);
+
 /* Rank-revealing LU with full pivot search (Algorithm 2, its garbles read as: the second
  * swap exchanges J_j; the loop stops before accepting a pivot; L and U are unit
  * triangular): greedy argmax |S| over the unused rows and columns, ties to the lowest

@@ -47,9 +47,21 @@ class AciStats(C.Structure):
                 ("device_ms", C.c_double), ("kernel_launches", C.c_int64),
                 ("ranks", C.POINTER(C.c_int64)), ("eps", C.POINTER(C.c_double)),
                 ("pivot_rows", C.POINTER(C.c_int32)), ("pivot_cols", C.POINTER(C.c_int32)),
-                ("kernel_ms", C.c_double * 4), ("kernel_count", C.c_int64 * 4), ("kernel_flops", C.c_double * 4)]
+                ("kernel_ms", C.c_double * 4), ("kernel_count", C.c_int64 * 4), ("kernel_flops", C.c_double * 4),
+                ("tensor_flops", C.c_double * 4)]
 
 KERNEL_CLASSES = ("frame", "pi", "pivot", "other")
+
+# aci_precision: "fp64", or "bf16xS" for S = 2..8 exact BF16 digit planes on the tensor cores.
+PRECISIONS = {"fp64": 0, **{f"bf16x{s}": s for s in range(2, 9)}}
+
+
+def _precision_code(p) -> int:
+    if isinstance(p, str):
+        if p not in PRECISIONS:
+            raise ValueError(f"unknown precision {p!r}; expected one of {sorted(PRECISIONS)}")
+        return PRECISIONS[p]
+    return int(p)
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -57,7 +69,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 # Every symbol the headers declare; tests check the library exports each one.
 EXPORTS = ["aci_create", "aci_destroy", "aci_last_error", "aci_opts_default", "aci_elementwise",
-           "aci_elementwise_ex", "aci_tt_release", "aci_k_frame_gemm", "aci_k_pi_block", "aci_k_prrlu",
+           "aci_elementwise_ex", "aci_tt_release", "aci_k_frame_gemm", "aci_k_pi_block",
+           "aci_k_frame_gemm_prec", "aci_k_pi_block_prec", "aci_k_prrlu",
            "aci_k_tt_random", "aci_k_apply_pinv", "aci_k_prrlu_static", "aci_k_reciprocal"]
 
 _lib = None
@@ -90,8 +103,11 @@ def load_library(build_if_missing: bool = True) -> C.CDLL:
                                        C.POINTER(AciOpts), C.POINTER(AciTT), C.POINTER(AciStats)]
     lib.aci_tt_release.argtypes = [vp, C.POINTER(AciTT)]
     lib.aci_k_frame_gemm.argtypes = [vp, i32, vp, vp, i32, i32, i32, vp, vp, i32, i32, vp]
+    lib.aci_k_frame_gemm_prec.argtypes = [vp, i32, i32, vp, vp, i32, i32, i32, vp, vp, i32, i32, vp]
     lib.aci_k_pi_block.argtypes = [vp, i32, i32, C.POINTER(vp), C.POINTER(vp), i32, i32,
                                    C.POINTER(i32), AciOp, vp, C.POINTER(dbl)]
+    lib.aci_k_pi_block_prec.argtypes = [vp, i32, i32, i32, C.POINTER(vp), C.POINTER(vp), i32, i32,
+                                        C.POINTER(i32), AciOp, vp, C.POINTER(dbl)]
     lib.aci_k_prrlu.argtypes = [vp, i32, vp, i32, i32, dbl, i32, vp, vp, vp, vp, vp,
                                 C.POINTER(i32), C.POINTER(dbl)]
     lib.aci_k_tt_random.argtypes = [vp, i32, C.c_uint64, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(vp)]
@@ -215,9 +231,10 @@ class Context:
     # ------------------------------------------------------------ the method
     def elementwise(self, a, b=None, op="mul", tol=1e-10, max_rank=64, *, tol_kind="rel",
                     max_sweeps=20, seed=0, init=None, coef=None, out_memory="device",
-                    pivots=False, profile=False):
+                    pivots=False, profile=False, precision="fp64"):
         """y ~ f(a, b) by ACI. ``a``/``b``: lists of cores (torch CUDA tensors, or numpy arrays
-        for host memory). Returns (cores, stats dict)."""
+        for host memory). ``precision``: "fp64" or "bf16xS" (S = 2..8 digit planes) for the
+        frame and Pi contractions. Returns (cores, stats dict)."""
         import torch
         A = _TTArg(a)
         Bt = _TTArg(b) if b is not None else None
@@ -228,6 +245,7 @@ class Context:
         opts.seed = int(seed)
         opts.out_memory = ACI_MEM_HOST if out_memory == "host" else ACI_MEM_DEVICE
         opts.profile = 1 if profile else 0
+        opts.precision = _precision_code(precision)
         It = None
         if init is not None:
             It = _TTArg(init)
@@ -272,7 +290,8 @@ class Context:
                     ranks=[int(ranks[i]) for i in range(L + 1)],
                     eps=[float(eps[i]) for i in range(max(L - 1, 0))],
                     kernels={k: dict(ms=stats.kernel_ms[i], count=int(stats.kernel_count[i]),
-                                     flops=stats.kernel_flops[i]) for i, k in enumerate(KERNEL_CLASSES)})
+                                     flops=stats.kernel_flops[i], tensor_flops=stats.tensor_flops[i])
+                             for i, k in enumerate(KERNEL_CLASSES)})
         if pivots:
             info["pivot_rows"] = [[int(prow[b * max_rank + q]) for q in range(info["ranks"][b + 1])]
                                   for b in range(L - 1)]
@@ -281,20 +300,20 @@ class Context:
         return cores, info
 
     # ------------------------------------------------------------ step-level entry points
-    def frame_gemm(self, A, B, arows=None, bcols=None, M=None, K=None, N=None):
+    def frame_gemm(self, A, B, arows=None, bcols=None, M=None, K=None, N=None, precision="fp64"):
         """C = A[arows, :K] @ B[:K, bcols] on device tensors (A, B row-major 2-D)."""
         import torch
         M = int(arows.numel()) if arows is not None else (M or A.shape[0])
         N = int(bcols.numel()) if bcols is not None else (N or B.shape[1])
         K = K or A.shape[1]
         Cm = torch.empty((M, N), dtype=A.dtype, device=A.device)
-        self._check(self.lib.aci_k_frame_gemm(
-            self.handle, _dtype_code(A), A.data_ptr(), arows.data_ptr() if arows is not None else None,
+        self._check(self.lib.aci_k_frame_gemm_prec(
+            self.handle, _dtype_code(A), _precision_code(precision), A.data_ptr(), arows.data_ptr() if arows is not None else None,
             M, K, A.shape[1], B.data_ptr(), bcols.data_ptr() if bcols is not None else None, N, B.shape[1],
             Cm.data_ptr()))
         return Cm
 
-    def pi_block(self, As, Bs, op="mul", coef=None):
+    def pi_block(self, As, Bs, op="mul", coef=None, precision="fp64"):
         """Pi = f(A^0 B^0, A^1 B^1) entrywise; returns (Pi, max|Pi|)."""
         import torch
         n = len(As)
@@ -304,8 +323,9 @@ class Context:
         Bp = (C.c_void_p * n)(*[b.data_ptr() for b in Bs])
         Ks = (C.c_int32 * n)(*[a.shape[1] for a in As])
         mx = C.c_double()
-        self._check(self.lib.aci_k_pi_block(self.handle, _dtype_code(As[0]), n, Ap, Bp, M, N, Ks,
-                                            make_op(op, coef), Pi.data_ptr(), C.byref(mx)))
+        self._check(self.lib.aci_k_pi_block_prec(self.handle, _dtype_code(As[0]), _precision_code(precision),
+                                                 n, Ap, Bp, M, N, Ks, make_op(op, coef), Pi.data_ptr(),
+                                                 C.byref(mx)))
         return Pi, mx.value
 
     def prrlu(self, M, tau, chimax, with_lu=True):

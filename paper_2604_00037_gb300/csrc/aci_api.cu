@@ -110,6 +110,10 @@ void note_launch(aci_ctx* ctx, const char* what) {
     ck(ctx, cudaGetLastError(), what);
 }
 
+bool valid_precision(int p) {
+    return p == ACI_PREC_FP64 || (p >= aci::kTcMinDigits && p <= aci::kTcMaxDigits);
+}
+
 long long sat_mul(long long a, long long b, long long cap) {
     if (a >= cap || b >= cap) return cap;
     long long v = a * b;
@@ -140,10 +144,11 @@ struct Run {
     aci_ctx* ctx;
     cudaStream_t st;
     int L = 0, N = 0, chimax = 0, maxit = 20, rel = 1, prof = 0;
+    int digits = 0;            // 0: FP64 contractions; 2..8: BF16 digit planes on the tensor cores
     // per-kernel-class accounting (aci_kernel_class)
     double kms[4] = {0, 0, 0, 0};
     long long kcount[4] = {0, 0, 0, 0};
-    double* kflops = nullptr;  // device [4]
+    double* kflops = nullptr;  // device [4]: algorithmic flops, then [4] tensor-core flops
     struct Pend {
         int cls;
         cudaEvent_t a, b;
@@ -215,6 +220,8 @@ struct Run {
     T* gpart = nullptr;                 // GEMM partial tiles
     int* gcount = nullptr;              // GEMM per-tile counters (kept zeroed)
     size_t gpart_elems = 1, gcount_n = 1;
+    unsigned char* tcbuf = nullptr;     // digit planes and scales of the tensor-core contractions
+    size_t tc_bytes = 0;
     unsigned long long* ll = nullptr;  // pivot-search exchange words
     size_t ll_words = 0;
     unsigned int prrlu_launches = 0;   // launches since the exchange area was last cleared
@@ -286,7 +293,7 @@ struct Run {
         eps_lr = c.take<double>(std::max(nb, 1));
         eps_rl = c.take<double>(std::max(nb, 1));
         eps_junk = c.take<double>(1);
-        kflops = c.take<double>(4);
+        kflops = c.take<double>(8);
         smax = c.take<unsigned long long>(1);
         initmax = c.take<unsigned long long>(1);
         flags = c.take<aci::IterFlags>(1);
@@ -295,6 +302,7 @@ struct Run {
         ll = c.take<unsigned long long>(ll_words);
         gpart = c.take<T>(gpart_elems);
         gcount = c.take<int>(gcount_n);
+        tcbuf = c.take<unsigned char>(tc_bytes);
         bonds_dev = c.take<aci::BondBuf<T>>(std::max(nb, 1));
         Yptr_dev = c.take<T*>(L);
         pcol_dev = c.take<int*>(std::max(nb, 1));
@@ -340,13 +348,19 @@ struct Run {
             if ((long long)mcap[b] * ncap[b] >= (1LL << 31))
                 fail(ctx, ACI_E_SHAPE, "a Pi block would exceed 2^31 entries");
         }
-        auto need = [&](int Mm, int Nm, int nprod, int combine) {
-            gpart_elems = std::max(gpart_elems, aci::gemm_part_elems(Mm, Nm, nprod, combine, ctx->num_sms));
-            gcount_n = std::max(gcount_n, aci::gemm_tile_counters(Mm, Nm, nprod));
-        };
         int rmax = 1;
         for (int n = 0; n < N; ++n)
             for (int s = 0; s <= L; ++s) rmax = std::max(rmax, r[n][s]);
+        for (int s = 0; s <= L; ++s) rmax = std::max(rmax, ry[s]);
+        auto need = [&](int Mm, int Nm, int nprod, int combine) {
+            gpart_elems = std::max(gpart_elems, aci::gemm_part_elems(Mm, Nm, nprod, combine, ctx->num_sms));
+            gcount_n = std::max(gcount_n, aci::gemm_tile_counters(Mm, Nm, nprod));
+            if (digits) {  // K of every contraction is an input rank or an initial-guess rank
+                const aci::TcPlan p = aci::tc_plan(digits, is_cplx, Mm, Nm, rmax, nprod, combine);
+                if (!p.ok) fail(ctx, ACI_E_SHAPE, "contraction too large for the digit-plane precision");
+                tc_bytes = std::max(tc_bytes, aci::tc_scratch_bytes(p));
+            }
+        };
         const int dmax = *std::max_element(d.begin(), d.end());
         for (int b = 0; b < nb; ++b) need(mcap[b], ncap[b], N, 1);
         for (int s = 0; s < L; ++s) {
@@ -366,7 +380,8 @@ struct Run {
     }
 
     // ---------------------------------------------------------------- launches
-    void gemm(aci::GemmArgs<T>& g, int Mmax, int Nmax, const char* what, int cls) {
+    // Kmax: the largest K of the products (a host-known input or initial-guess rank).
+    void gemm(aci::GemmArgs<T>& g, int Mmax, int Nmax, int Kmax, const char* what, int cls) {
         g.chi = chi;
         g.flops = flops_of(cls);
         g.part = gpart;
@@ -374,8 +389,21 @@ struct Run {
         g.target_units = aci::gemm_target_units(ctx->num_sms);
         g.num_sms = ctx->num_sms;
         cudaEvent_t e = pre(cls);
-        aci::launch_gemm<T>(g, Mmax, Nmax, st);
+        if (digits) {
+            ck(ctx, aci::launch_gemm_tc<T>(g, Mmax, Nmax, Kmax, digits, tcbuf, tc_bytes, err,
+                                           prof ? kflops + 4 + cls : nullptr, st),
+               what);
+            ctx->launches++;  // digit split + tensor-core contraction
+            kcount[cls]++;
+        } else {
+            aci::launch_gemm<T>(g, Mmax, Nmax, st);
+        }
         post(cls, e, what);
+    }
+    int kmax_of(int s) const {  // largest input rank at bond position s
+        int k = 1;
+        for (int n = 0; n < N; ++n) k = std::max(k, r[n][s]);
+        return k;
     }
 
     aci::GemmArgs<T> gemm_base() {
@@ -437,7 +465,7 @@ struct Run {
         g.N[0] = dimr(d[b + 1], b + 2);
         g.C[0] = Pi[b];
         g.smax = smax;
-        gemm(g, mcap[b], ncap[b], "pi_block", ACI_KCLASS_PI);
+        gemm(g, mcap[b], ncap[b], kmax_of(b + 1), "pi_block", ACI_KCLASS_PI);
     }
 
     // LX[n][b] = rows prow[b-1] of LX[n][b-1], times X^n_b (Leftframe of Algorithm 5).
@@ -459,7 +487,7 @@ struct Run {
             nmax = std::max(nmax, d[b] * r[n][b + 1]);
         }
         g.arow = prow[b - 1];
-        gemm(g, cap[b], nmax, "left_half", ACI_KCLASS_FRAME);
+        gemm(g, cap[b], nmax, kmax_of(b), "left_half", ACI_KCLASS_FRAME);
     }
 
     // XR[n][s] = X^n_s times columns pcol[s] of XR[n][s+1] (Rightframe of Algorithm 5).
@@ -481,7 +509,7 @@ struct Run {
             mmax = std::max(mmax, r[n][s] * d[s]);
         }
         g.bcol = pcol[s];
-        gemm(g, mmax, cap[s + 1], "right_half", ACI_KCLASS_FRAME);
+        gemm(g, mmax, cap[s + 1], kmax_of(s + 1), "right_half", ACI_KCLASS_FRAME);
     }
 
     // ---------------------------------------------------------------- Algorithm 1
@@ -516,7 +544,7 @@ struct Run {
         ck(ctx, cudaMemcpyAsync(dd, d.data(), sizeof(int) * L, cudaMemcpyHostToDevice, st), "init d");
         ck(ctx, cudaMemsetAsync(err, 0, sizeof(int), st), "memset");
         ck(ctx, cudaMemsetAsync(smax, 0, sizeof(unsigned long long), st), "memset");
-        ck(ctx, cudaMemsetAsync(kflops, 0, 4 * sizeof(double), st), "memset");
+        ck(ctx, cudaMemsetAsync(kflops, 0, 8 * sizeof(double), st), "memset");
         ck(ctx, cudaMemsetAsync(ll, 0, ll_words * sizeof(unsigned long long), st), "clear exchange");
         prrlu_launches = 0;
         ck(ctx, cudaMemsetAsync(gcount, 0, gcount_n * sizeof(int), st), "clear counters");
@@ -560,7 +588,7 @@ struct Run {
             g.N[0] = dimc(1);
             g.C[0] = Ysc[0];
             g.smax = smax;
-            gemm(g, d[0], 1, "single_site", ACI_KCLASS_PI);
+            gemm(g, d[0], 1, 1, "single_site", ACI_KCLASS_PI);
             return finish(out, stats, out_memory, 0, 1, 0, launches0);
         }
 
@@ -608,7 +636,7 @@ struct Run {
                 g.bcol = pcol[s];
             }
             g.smax = initmax;
-            gemm(g, ry[s] * d[s], cap[s + 1], "init_gemm", ACI_KCLASS_OTHER);
+            gemm(g, ry[s] * d[s], cap[s + 1], ry[s + 1], "init_gemm", ACI_KCLASS_OTHER);
             prrlu(Ms, dimc(ry[s]), dimr(d[s], s + 1), ry[s], d[s] * cap[s + 1], s, s - 1, false,
                   eps_junk, initmax);
             right_half(s);
@@ -705,7 +733,7 @@ struct Run {
             ck(ctx, cudaStreamSynchronize(st), "sweep");
             fl = *ctx->hflags;
             harvest(gexec != nullptr);
-            if (fl.err & aci::DEVERR_TIMEOUT) fail(ctx, ACI_E_TIMEOUT, "a device-side wait in the pivot search timed out");
+            if (fl.err & aci::DEVERR_TIMEOUT) fail(ctx, ACI_E_TIMEOUT, "a device-side wait timed out");
             if ((fl.err & aci::DEVERR_NUMERIC) || !(fl.S < INFINITY))
                 fail(ctx, ACI_E_NUMERIC, "a non-finite value reached the pivot search");
             const double tau = rel ? tol * fl.S : tol;
@@ -744,7 +772,7 @@ struct Run {
         ck(ctx, cudaStreamSynchronize(st), "finish");
         int errflag = 0;
         ck(ctx, cudaMemcpy(&errflag, err, sizeof(int), cudaMemcpyDeviceToHost), "read err");
-        if (errflag & aci::DEVERR_TIMEOUT) fail(ctx, ACI_E_TIMEOUT, "a device-side wait in the pivot search timed out");
+        if (errflag & aci::DEVERR_TIMEOUT) fail(ctx, ACI_E_TIMEOUT, "a device-side wait timed out");
         if (errflag & aci::DEVERR_NUMERIC) fail(ctx, ACI_E_NUMERIC, "a non-finite value reached the pivot search");
         // allocate and fill the output TT
         int32_t* od = static_cast<int32_t*>(std::malloc(sizeof(int32_t) * L));
@@ -801,12 +829,13 @@ struct Run {
             stats->device_ms = ms;
             stats->kernel_launches = ctx->launches - launches0;
             harvest();
-            double fl_h[4] = {0, 0, 0, 0};
+            double fl_h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             if (prof) ck(ctx, cudaMemcpy(fl_h, kflops, sizeof(fl_h), cudaMemcpyDeviceToHost), "flops");
             for (int q = 0; q < 4; ++q) {
                 stats->kernel_ms[q] = kms[q];
                 stats->kernel_count[q] = kcount[q];
                 stats->kernel_flops[q] = fl_h[q];
+                stats->tensor_flops[q] = fl_h[4 + q];
             }
             if (stats->ranks)
                 for (int s = 0; s <= L; ++s) stats->ranks[s] = chi_h[s];
@@ -857,6 +886,7 @@ aci_status run_typed(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, 
     R.rel = o.tol_kind == ACI_TOL_REL;
     R.maxit = o.max_sweeps;
     R.prof = o.profile ? 1 : 0;
+    R.digits = o.precision;
     R.seed = o.seed;
     R.op = make_op<T>(op);
     R.init = o.init;
@@ -940,7 +970,7 @@ aci_status aci_elementwise_ex(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, ac
         if (o.tol_kind != ACI_TOL_REL && o.tol_kind != ACI_TOL_ABS) fail(ctx, ACI_E_ARG, "bad tol_kind");
         if (o.max_sweeps < 1) fail(ctx, ACI_E_ARG, "max_sweeps must be >= 1");
         if (o.pivot_mode != ACI_PIVOT_FULL) fail(ctx, ACI_E_ARG, "unsupported pivot mode");
-        if (o.precision != ACI_PREC_FP64) fail(ctx, ACI_E_ARG, "unsupported precision");
+        if (!valid_precision(o.precision)) fail(ctx, ACI_E_ARG, "unsupported precision");
         if (o.out_memory != ACI_MEM_DEVICE && o.out_memory != ACI_MEM_HOST) fail(ctx, ACI_E_ARG, "bad out_memory");
         validate_tt(ctx, a, "a");
         const bool unary = op.kind == ACI_OP_ABS2_MUL;
@@ -999,22 +1029,43 @@ aci_status aci_tt_release(aci_ctx* ctx, aci_tt* out) {
 
 // ---------------------------------------------------------------- step-level entry points
 
-aci_status aci_k_frame_gemm(aci_ctx* ctx, int32_t dtype, const void* A, const int32_t* arows, int32_t M, int32_t K,
-                            int32_t lda, const void* B, const int32_t* bcols, int32_t N, int32_t ldb, void* C) {
+aci_status aci_k_frame_gemm_prec(aci_ctx* ctx, int32_t dtype, int32_t precision, const void* A, const int32_t* arows,
+                                 int32_t M, int32_t K, int32_t lda, const void* B, const int32_t* bcols, int32_t N,
+                                 int32_t ldb, void* C) {
     if (!ctx) return ACI_E_ARG;
     ctx->err.clear();
     try {
         if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < 1) fail(ctx, ACI_E_ARG, "bad arguments");
+        if (!valid_precision(precision)) fail(ctx, ACI_E_ARG, "unsupported precision");
         ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
         auto go = [&](auto tag) {
             using T = decltype(tag);
             const size_t np = aci::gemm_part_elems(M, N, 1, 0, ctx->num_sms);
             const size_t nc = aci::gemm_tile_counters(M, N, 1);
-            char* ws = workspace(ctx, 512 + np * sizeof(T) + nc * sizeof(int));
-            int* dummy = reinterpret_cast<int*>(ws);
-            T* part = reinterpret_cast<T*>(ws + 256);
-            int* cnt = reinterpret_cast<int*>(ws + 256 + np * sizeof(T));
+            aci::TcPlan tp;
+            size_t tcb = 0;
+            if (precision) {
+                tp = aci::tc_plan(precision, sizeof(T) == sizeof(cplx), M, N, K, 1, 0);
+                if (!tp.ok) fail(ctx, ACI_E_SHAPE, "contraction too large for the digit-plane precision");
+                tcb = aci::tc_scratch_bytes(tp);
+            }
+            Carver c;
+            int *dummy, *cnt, *er;
+            T* part;
+            unsigned char* tcbuf;
+            auto lay = [&](Carver& cv) {
+                dummy = cv.take<int>(1);
+                er = cv.take<int>(1);
+                cnt = cv.take<int>(nc);
+                part = cv.take<T>(np);
+                tcbuf = cv.take<unsigned char>(tcb);
+            };
+            lay(c);
+            Carver c2;
+            c2.base = workspace(ctx, c.off);
+            lay(c2);
             ck(ctx, cudaMemsetAsync(cnt, 0, nc * sizeof(int), ctx->stream), "memset");
+            ck(ctx, cudaMemsetAsync(er, 0, sizeof(int), ctx->stream), "memset");
             aci::GemmArgs<T> g;
             std::memset(&g, 0, sizeof(g));
             g.part = part;
@@ -1033,46 +1084,86 @@ aci_status aci_k_frame_gemm(aci_ctx* ctx, int32_t dtype, const void* A, const in
             g.bcol = bcols;
             g.chi = dummy;
             g.nprod = 1;
-            aci::launch_gemm<T>(g, M, N, ctx->stream);
+            if (precision) {
+                ck(ctx, aci::launch_gemm_tc<T>(g, M, N, K, precision, tcbuf, tcb, er, nullptr, ctx->stream),
+                   "frame_gemm");
+                ctx->launches++;
+            } else {
+                aci::launch_gemm<T>(g, M, N, ctx->stream);
+            }
+            note_launch(ctx, "frame_gemm");
+            int errflag = 0;
+            ck(ctx, cudaMemcpyAsync(&errflag, er, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "err");
+            ck(ctx, cudaStreamSynchronize(ctx->stream), "frame_gemm");
+            if (errflag & aci::DEVERR_TIMEOUT) fail(ctx, ACI_E_TIMEOUT, "a device-side wait timed out");
         };
         if (dtype == ACI_R64) go(double());
         else if (dtype == ACI_C128) go(cplx());
         else fail(ctx, ACI_E_DTYPE, "unsupported dtype");
-        note_launch(ctx, "frame_gemm");
-        ck(ctx, cudaStreamSynchronize(ctx->stream), "frame_gemm");
         return ACI_OK;
     } catch (Fail& f) {
         return f.st;
     }
 }
 
-aci_status aci_k_pi_block(aci_ctx* ctx, int32_t dtype, int32_t nprod, const void* const* A, const void* const* B,
-                          int32_t M, int32_t N, const int32_t* K, aci_op op, void* Pi, double* maxabs) {
+aci_status aci_k_frame_gemm(aci_ctx* ctx, int32_t dtype, const void* A, const int32_t* arows, int32_t M, int32_t K,
+                            int32_t lda, const void* B, const int32_t* bcols, int32_t N, int32_t ldb, void* C) {
+    return aci_k_frame_gemm_prec(ctx, dtype, ACI_PREC_FP64, A, arows, M, K, lda, B, bcols, N, ldb, C);
+}
+
+aci_status aci_k_pi_block_prec(aci_ctx* ctx, int32_t dtype, int32_t precision, int32_t nprod, const void* const* A,
+                               const void* const* B, int32_t M, int32_t N, const int32_t* K, aci_op op, void* Pi,
+                               double* maxabs) {
     if (!ctx) return ACI_E_ARG;
     ctx->err.clear();
     try {
         if (!A || !B || !K || !Pi || M < 1 || N < 1 || nprod < 1 || nprod > 2) fail(ctx, ACI_E_ARG, "bad arguments");
         if (op.kind < ACI_OP_MUL || op.kind > ACI_OP_AFFINE) fail(ctx, ACI_E_ARG, "unknown op kind");
+        if (!valid_precision(precision)) fail(ctx, ACI_E_ARG, "unsupported precision");
+        int kmax = 1;
+        for (int n = 0; n < nprod; ++n) {
+            if (K[n] < 1) fail(ctx, ACI_E_ARG, "K must be >= 1");
+            kmax = std::max(kmax, (int)K[n]);
+        }
         ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
-        const size_t np = aci::gemm_part_elems(M, N, nprod, 1, ctx->num_sms);
-        const size_t nc = aci::gemm_tile_counters(M, N, nprod);
-        char* ws = workspace(ctx, 1024 + np * sizeof(cplx) + nc * sizeof(int));
-        int* dummy = reinterpret_cast<int*>(ws);
-        unsigned long long* smax = reinterpret_cast<unsigned long long*>(ws + 256);
-        int* cnt = reinterpret_cast<int*>(ws + 512);
-        void* part_raw = ws + 512 + ((nc * sizeof(int) + 255) & ~(size_t)255);
-        ck(ctx, cudaMemsetAsync(smax, 0, 8, ctx->stream), "memset");
-        ck(ctx, cudaMemsetAsync(cnt, 0, nc * sizeof(int), ctx->stream), "memset");
         auto go = [&](auto tag) {
             using T = decltype(tag);
+            const size_t np = aci::gemm_part_elems(M, N, nprod, 1, ctx->num_sms);
+            const size_t nc = aci::gemm_tile_counters(M, N, nprod);
+            aci::TcPlan tp;
+            size_t tcb = 0;
+            if (precision) {
+                tp = aci::tc_plan(precision, sizeof(T) == sizeof(cplx), M, N, kmax, nprod, 1);
+                if (!tp.ok) fail(ctx, ACI_E_SHAPE, "contraction too large for the digit-plane precision");
+                tcb = aci::tc_scratch_bytes(tp);
+            }
+            int *dummy, *cnt, *er;
+            unsigned long long* smax;
+            T* part;
+            unsigned char* tcbuf;
+            auto lay = [&](Carver& cv) {
+                dummy = cv.take<int>(1);
+                er = cv.take<int>(1);
+                smax = cv.take<unsigned long long>(1);
+                cnt = cv.take<int>(nc);
+                part = cv.take<T>(np);
+                tcbuf = cv.take<unsigned char>(tcb);
+            };
+            Carver c;
+            lay(c);
+            Carver c2;
+            c2.base = workspace(ctx, c.off);
+            lay(c2);
+            ck(ctx, cudaMemsetAsync(smax, 0, 8, ctx->stream), "memset");
+            ck(ctx, cudaMemsetAsync(er, 0, sizeof(int), ctx->stream), "memset");
+            ck(ctx, cudaMemsetAsync(cnt, 0, nc * sizeof(int), ctx->stream), "memset");
             aci::GemmArgs<T> g;
             std::memset(&g, 0, sizeof(g));
-            g.part = static_cast<T*>(part_raw);
+            g.part = part;
             g.tile_count = cnt;
             g.target_units = aci::gemm_target_units(ctx->num_sms);
             g.num_sms = ctx->num_sms;
             for (int n = 0; n < nprod; ++n) {
-                if (K[n] < 1) fail(ctx, ACI_E_ARG, "K must be >= 1");
                 g.A[n] = static_cast<const T*>(A[n]);
                 g.B[n] = static_cast<const T*>(B[n]);
                 g.K[n] = dimc(K[n]);
@@ -1087,20 +1178,34 @@ aci_status aci_k_pi_block(aci_ctx* ctx, int32_t dtype, int32_t nprod, const void
             g.combine = 1;
             g.op = make_op<T>(op);
             g.smax = smax;
-            aci::launch_gemm<T>(g, M, N, ctx->stream);
+            if (precision) {
+                ck(ctx, aci::launch_gemm_tc<T>(g, M, N, kmax, precision, tcbuf, tcb, er, nullptr, ctx->stream),
+                   "pi_block");
+                ctx->launches++;
+            } else {
+                aci::launch_gemm<T>(g, M, N, ctx->stream);
+            }
+            note_launch(ctx, "pi_block");
+            unsigned long long bits = 0;
+            int errflag = 0;
+            ck(ctx, cudaMemcpyAsync(&bits, smax, 8, cudaMemcpyDeviceToHost, ctx->stream), "maxabs");
+            ck(ctx, cudaMemcpyAsync(&errflag, er, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "err");
+            ck(ctx, cudaStreamSynchronize(ctx->stream), "pi_block");
+            if (errflag & aci::DEVERR_TIMEOUT) fail(ctx, ACI_E_TIMEOUT, "a device-side wait timed out");
+            if (maxabs) std::memcpy(maxabs, &bits, 8);
         };
         if (dtype == ACI_R64) go(double());
         else if (dtype == ACI_C128) go(cplx());
         else fail(ctx, ACI_E_DTYPE, "unsupported dtype");
-        note_launch(ctx, "pi_block");
-        unsigned long long bits = 0;
-        ck(ctx, cudaMemcpyAsync(&bits, smax, 8, cudaMemcpyDeviceToHost, ctx->stream), "maxabs");
-        ck(ctx, cudaStreamSynchronize(ctx->stream), "pi_block");
-        if (maxabs) std::memcpy(maxabs, &bits, 8);
         return ACI_OK;
     } catch (Fail& f) {
         return f.st;
     }
+}
+
+aci_status aci_k_pi_block(aci_ctx* ctx, int32_t dtype, int32_t nprod, const void* const* A, const void* const* B,
+                          int32_t M, int32_t N, const int32_t* K, aci_op op, void* Pi, double* maxabs) {
+    return aci_k_pi_block_prec(ctx, dtype, ACI_PREC_FP64, nprod, A, B, M, N, K, op, Pi, maxabs);
 }
 
 aci_status aci_k_prrlu(aci_ctx* ctx, int32_t dtype, const void* Min, int32_t m, int32_t n, double tau, int32_t chimax,

@@ -32,6 +32,46 @@ int gemm_target_units(int num_sms);
 size_t gemm_part_elems(int Mmax, int Nmax, int nprod, int combine, int num_sms);
 size_t gemm_tile_counters(int Mmax, int Nmax, int nprod);
 
+// Tensor-core form of the same contractions (exact BF16 digit planes, FP32 accumulation in tensor
+// memory): the operands and results of GemmArgs plus the digit-plane scratch.
+constexpr int kTcMinDigits = 2;
+constexpr int kTcMaxDigits = 8;
+
+template <class T> struct TcArgs {
+    const T* A[2];
+    const T* B[2];
+    T* C[2];
+    DimE M[2], N[2], K[2], lda[2], ldb[2];
+    const int* arow;
+    const int* bcol;
+    const int* chi;
+    int nprod, combine;
+    OpParams<T> op;
+    unsigned long long* smax;
+    double* flops;     // FP64-equivalent algorithmic flops (as gemm_kernel)
+    double* tc_flops;  // optional: BF16 tensor-core flops issued
+    int* err;
+    int S, bits, NT, ksl, mtiles, ntiles, nst;
+    uint32_t tmem_cols;
+    unsigned char* planesA;  // [nprod][S][mtiles][ksl] slabs of 128 x 16 BF16
+    unsigned char* planesB;  // [nprod][S][ntiles][ksl] slabs of NT x 16 BF16
+    int* expoA;              // [nprod][mtiles * 128] row scale exponents
+    int* expoB;              // [nprod][ntiles * NT] column scale exponents
+};
+
+struct TcPlan {
+    int S, bits, NT, nacc, ksl, mtiles, ntiles, nst;
+    uint32_t tmem_cols;
+    size_t bytesA, bytesB, bytesE, smem;
+    bool ok;
+};
+// Kmax: largest K of the launch's products (complex counts once; the plan doubles it).
+TcPlan tc_plan(int digits, bool cplx_values, int Mmax, int Nmax, int Kmax, int nprod, int combine);
+size_t tc_scratch_bytes(const TcPlan& p);
+template <class T>
+cudaError_t launch_gemm_tc(const GemmArgs<T>& g, int Mmax, int Nmax, int Kmax, int digits, void* scratch,
+                           size_t scratch_bytes, int* err, double* tc_flops, cudaStream_t st);
+
 template <class T> struct PrrluArgs {
     const T* Min;       // m x n row-major input, not modified
     DimE m, n;          // live shape (device-resolved)
