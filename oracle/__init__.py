@@ -12,14 +12,14 @@ in each module's header.
 """
 
 from .algorithms import (
-    aci, ldu, crossinterpolate, localupdate, leftframe, rightframe, apply_op,
+    aci, ldu, ldu_rook, factorise, crossinterpolate, localupdate, leftframe, rightframe, apply_op,
     magnitude, pivot_key, init_guess, assemble_output, pi_tensor,
 )
 from .hadamard import hadamard_kron, tt_round_svd
 from .rng import splitmix64_uniform, random_tt_counter
 
 __all__ = [
-    "aci", "ldu", "crossinterpolate", "localupdate", "leftframe", "rightframe",
+    "aci", "ldu", "ldu_rook", "factorise", "crossinterpolate", "localupdate", "leftframe", "rightframe",
     "apply_op", "magnitude", "pivot_key", "init_guess", "assemble_output", "pi_tensor",
     "hadamard_kron", "tt_round_svd", "splitmix64_uniform", "random_tt_counter",
 ]

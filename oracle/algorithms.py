@@ -35,6 +35,18 @@ Readings of places where the paper is silent or garbled:
       set of the previous one is a fixed point (the next sweep would repeat it exactly).
   R9  Y^init is the counter-based SplitMix64 TT of oracle.rng with ranks
       min(chi_hat, min_n r^n_s, prod_{t<s} d_t, prod_{t>=s} d_t), unless the caller passes one.
+  R10 (reserved)
+  R11 Rook search (pivot_mode="rook"; not written in the paper, whose O(d chi'^3) cost per
+      update in App. A fits a partial search): the residual R_p = M - sum_{q<p} L_q D_q U_q
+      is formed lazily, one column or row at a time. Step 0 starts from the column of the
+      global argmax of |M|; step p >= 1 from the column of the largest residual of the
+      previous pivot row (before its elimination) among unused columns. From column c0:
+      r1 = argmax_r |R(r,c0)|, c1 = argmax_c |R(r1,c)|; c1 == c0 accepts (r1, c0); else
+      r2 = argmax_r |R(r,c1)|; r2 == r1 accepts (r1, c1); else (r2, c1) is accepted after
+      the fourth hop. Searches run over unused rows / columns with the key and tie rule of
+      R4 (lowest index). The pivot value is taken from the column evaluation; L's column is
+      the residual column over the pivot, U's row the residual row over the pivot. The stop
+      test and epsilon are those of R2 with the rook pivot in place of the block maximum.
 
 Parity pins (tests/test_oracle_*.py): LDU against an independent complete-pivoting LU
 and brute-force residual identities; CI factors against exact interpolation on the
@@ -159,6 +171,115 @@ def ldu(M, tau: float, chimax: int):
                 best=np.array(best_list), second=np.array(second_list))
 
 
+def _argmax_free(key, free):
+    """Index of the largest key among free entries (ties to the lowest index), its key and the
+    next-largest free key (-inf if none)."""
+    k = np.where(free, key, -np.inf)
+    i = int(np.argmax(k))  # first occurrence: the lowest index among exact ties
+    rest = k.copy()
+    rest[i] = -np.inf
+    return i, float(k[i]), float(rest.max()) if rest.size > 1 else -np.inf
+
+
+def ldu_rook(M, tau: float, chimax: int):
+    """Rook-search prrLU (reading R11): the factors, stop test and outputs of ldu() with each
+    pivot found by alternating row and column searches of the lazily formed residual."""
+    M = np.array(M, copy=True)
+    m, n = M.shape
+    cplx = np.iscomplexobj(M)
+    kcap = min(m, n, chimax)
+    L = np.zeros((m, kcap), dtype=M.dtype)
+    U = np.zeros((kcap, n), dtype=M.dtype)
+    D = np.zeros(kcap, dtype=M.dtype)
+    free_r = np.ones(m, dtype=bool)
+    free_c = np.ones(n, dtype=bool)
+    I, J = [], []
+    best_list, second_list = [], []
+    eps = 0.0
+    p = 0
+    c_next = None
+
+    def mag_of_key(k):
+        if not np.isfinite(k):
+            return k
+        return np.sqrt(k) if cplx else k
+
+    def resid_col(c):
+        return M[:, c] - L[:, :p] @ (D[:p] * U[:p, c])
+
+    def resid_row(r):
+        return M[r, :] - (L[r, :p] * D[:p]) @ U[:p, :]
+
+    while True:
+        if p == min(m, n):
+            eps = 0.0
+            break
+        gaps = []
+        if p == 0:  # the column of the global argmax of |M| (R4 ties: lowest row * n + col)
+            key = pivot_key(M)
+            flat = key.reshape(-1)
+            c0 = int(np.argmax(flat)) % n
+            srt = np.sort(flat)
+            if flat.size > 1:
+                gaps.append(mag_of_key(srt[-1]) - mag_of_key(srt[-2]))
+        else:
+            c0 = c_next
+        col = resid_col(c0)
+        r1, k1, k1b = _argmax_free(pivot_key(col), free_r)
+        row = resid_row(r1)
+        c1, k2, k2b = _argmax_free(pivot_key(row), free_c)
+        gaps += [mag_of_key(k1) - mag_of_key(k1b), mag_of_key(k2) - mag_of_key(k2b)]
+        if c1 == c0:
+            r, c = r1, c0
+        else:
+            col = resid_col(c1)
+            r2, k3, k3b = _argmax_free(pivot_key(col), free_r)
+            gaps.append(mag_of_key(k3) - mag_of_key(k3b))
+            if r2 == r1:
+                r, c = r1, c1
+            else:
+                r, c = r2, c1
+                row = resid_row(r2)
+        piv = col[r]
+        mag = float(magnitude(piv))
+        if p == chimax or (p >= 1 and mag <= tau):
+            eps = mag
+            break
+        if piv != 0:
+            L[:, p] = np.where(free_r, col / piv, 0)
+            U[p, :] = np.where(free_c, row / piv, 0)
+        L[r, p] = 1
+        U[p, c] = 1
+        D[p] = piv
+        free_r[r] = False
+        free_c[c] = False
+        I.append(r)
+        J.append(c)
+        if free_c.any():  # the next start column: largest residual of this pivot row (R11)
+            c_next, kn, knb = _argmax_free(pivot_key(row), free_c)
+            gaps.append(mag_of_key(kn) - mag_of_key(knb))
+        best_list.append(mag)
+        g = [x for x in gaps if np.isfinite(x)]
+        second_list.append(mag - (min(g) if g else np.inf))
+        p += 1
+    k = p
+    return dict(L=L[:, :k].copy(), D=D[:k].copy(), U=U[:k, :].copy(), I=np.array(I, dtype=np.int64),
+                J=np.array(J, dtype=np.int64), eps=eps, k=k, best=np.array(best_list),
+                second=np.array(second_list))
+
+
+PIVOT_MODES = ("full", "rook")
+
+
+def factorise(M, tau: float, chimax: int, pivot_mode: str = "full"):
+    """Algorithm 2 with the full search, or the rook search of reading R11."""
+    if pivot_mode == "full":
+        return ldu(M, tau, chimax)
+    if pivot_mode == "rook":
+        return ldu_rook(M, tau, chimax)
+    raise ValueError(pivot_mode)
+
+
 # ---------------------------------------------------------------- Algorithm 3: CI
 
 def _inv_diag(D):
@@ -168,9 +289,9 @@ def _inv_diag(D):
     return out
 
 
-def crossinterpolate(M, tau: float, chimax: int, leftorright: str = "right"):
+def crossinterpolate(M, tau: float, chimax: int, leftorright: str = "right", pivot_mode: str = "full"):
     """Algorithm 3: A, B with A @ B = L D U ~ M; "left" puts P^-1 into A, "right" into B."""
-    f = ldu(M, tau, chimax)
+    f = factorise(M, tau, chimax, pivot_mode)
     L, D, U, I, J = f["L"], f["D"], f["U"], f["I"], f["J"]
     if leftorright == "left":
         LI = L[I, :]  # k x k unit lower
@@ -187,11 +308,11 @@ def crossinterpolate(M, tau: float, chimax: int, leftorright: str = "right"):
 
 # ---------------------------------------------------------------- Algorithm 4: local update
 
-def localupdate(Pi, tau: float, chimax: int, leftorright: str):
+def localupdate(Pi, tau: float, chimax: int, leftorright: str, pivot_mode: str = "full"):
     """Algorithm 4: reshape Pi[alpha, s, s', beta] to M[(alpha, s), (s', beta)] and factorise."""
     a, d1, d2, b = Pi.shape
     M = Pi.reshape(a * d1, d2 * b)
-    f = crossinterpolate(M, tau, chimax, leftorright)
+    f = crossinterpolate(M, tau, chimax, leftorright, pivot_mode)
     k = f["k"]
     f["Y"] = f["A"].reshape(a, d1, k)
     f["Y2"] = f["B"].reshape(k, d2, b)
@@ -272,7 +393,7 @@ def assemble_output(factors, L: int):
 
 def aci(inputs, op: str = "mul", tol: float = 1e-10, max_rank: int = 64, *,
         tol_kind: str = "rel", maxiter: int = 20, coef=None, init=None, seed: int = 0,
-        record: bool = False):
+        record: bool = False, pivot_mode: str = "full"):
     """Algorithm 1: alternating cross interpolation of f(X^1, ..., X^N).
 
     ``inputs`` is a list of N TTs (lists of cores (r, d, r')). Returns a dict with the
@@ -315,7 +436,7 @@ def aci(inputs, op: str = "mul", tol: float = 1e-10, max_rank: int = 64, *,
         r = Y[s].shape[0]
         M = Y[s].reshape(r, -1)
         tau0 = tol * _maxabs(M) if rel else tol
-        f = crossinterpolate(M, tau0, chimax, "right")
+        f = crossinterpolate(M, tau0, chimax, "right", pivot_mode)
         nj = len(J[s + 1])
         J[s] = [(int(q) // nj,) + J[s + 1][int(q) % nj] for q in f["J"]]
         Y[s] = f["B"].reshape(f["k"], dims[s], nj)
@@ -340,7 +461,7 @@ def aci(inputs, op: str = "mul", tol: float = 1e-10, max_rank: int = 64, *,
         Pi = fvals(blocks).astype(dt)
         S = max(S, _maxabs(Pi))
         tau = tol * S if rel else tol
-        f = localupdate(Pi, tau, chimax, direction)
+        f = localupdate(Pi, tau, chimax, direction, pivot_mode)
         ni = len(I[b - 1])
         nj = len(J[b + 2])
         I[b] = [I[b - 1][int(q) // dims[b]] + (int(q) % dims[b],) for q in f["I"]]

@@ -85,3 +85,95 @@ def test_planted_mistake_is_caught(kind, monkeypatch):
     except (KeyError, IndexError, ValueError, np.linalg.LinAlgError, FloatingPointError):
         return  # structurally broken: caught
     assert not (err <= 10 * p["tol"]), f"mutant {kind} passed the dense brute-force pin (err={err})"
+
+
+def _mutant_rook(kind):
+    """A copy of the rook search (reading R11) with one planted mistake."""
+
+    def ldu_rook(M, tau, chimax):
+        M = np.array(M, copy=True)
+        m, n = M.shape
+        kcap = min(m, n, chimax)
+        L = np.zeros((m, kcap))
+        U = np.zeros((kcap, n))
+        D = np.zeros(kcap)
+        fr = np.ones(m, bool)
+        fc = np.ones(n, bool)
+        I, J = [], []
+        p, c_next = 0, None
+        sgn = 1.0 if kind == "resid_sign" else -1.0
+
+        def col_of(c):
+            w = U[:p, c] if kind == "missing_D" else D[:p] * U[:p, c]
+            return M[:, c] + sgn * (L[:, :p] @ w)
+
+        def row_of(r):
+            v = L[r, :p] if kind == "missing_D" else L[r, :p] * D[:p]
+            return M[r, :] + sgn * (v @ U[:p, :])
+
+        def amax(v, free):
+            return int(np.argmax(np.where(free, np.abs(v), -1.0)))
+
+        while p < min(m, n):
+            c0 = int(np.argmax(np.abs(M))) % n if p == 0 else c_next
+            col = col_of(c0)
+            r1 = amax(col, fr)
+            row = row_of(r1)
+            c1 = amax(row, fc)
+            if c1 == c0:
+                r, c = r1, c0
+            elif kind == "no_second_hop":
+                r, c = r1, c1
+            else:
+                col = col_of(c1)
+                r2 = amax(col, fr)
+                r, c = (r1, c1) if r2 == r1 else (r2, c1)
+                if r != r1 and kind != "row_from_stale":
+                    row = row_of(r)
+            piv = col[r]
+            if p == chimax or (p >= 1 and abs(piv) <= tau):
+                break
+            L[:, p] = np.where(fr, col / piv, 0)
+            U[p, :] = np.where(fc, row / piv, 0)
+            L[r, p] = U[p, c] = 1
+            D[p] = piv
+            fr[r] = fc[c] = False
+            I.append(r)
+            J.append(c)
+            if fc.any():
+                c_next = int(np.argmax(np.where(fc, np.abs(row), -1.0)))
+            p += 1
+        return dict(L=L[:, :p], D=D[:p], U=U[:p], I=np.array(I), J=np.array(J), eps=0.0, k=p)
+
+    return ldu_rook
+
+
+def _rook_pin_fails(mut):
+    """The Schur-complement and cross-interpolation pins of test_oracle_rook."""
+    from tests.test_oracle_rook import schur
+    for seed in range(8):
+        rng = np.random.default_rng(seed)
+        M = rng.standard_normal((8, 7))
+        f = mut(M, 0.0, 6)
+        I, J = list(f["I"]), list(f["J"])
+        if len(set(I)) != len(I) or len(set(J)) != len(J):
+            return True
+        A = f["L"] @ (f["D"][:, None] * f["U"])
+        if np.abs(A[I, :] - M[I, :]).max() > 1e-10 or np.abs(A[:, J] - M[:, J]).max() > 1e-10:
+            return True
+        for p in range(f["k"]):
+            R = schur(M, I[:p], J[:p])
+            free = np.ones(8, bool)
+            free[I[:p]] = False
+            if abs(f["D"][p] - R[I[p], J[p]]) > 1e-9 or abs(R[I[p], J[p]]) < np.abs(R[free, J[p]]).max() * (1 - 1e-9):
+                return True
+    return False
+
+
+@pytest.mark.parametrize("kind", ["resid_sign", "missing_D", "no_second_hop", "row_from_stale"])
+def test_planted_rook_mistake_is_caught(kind):
+    assert _rook_pin_fails(_mutant_rook(kind)), f"rook mutant {kind} passed the pins"
+
+
+def test_unmutated_rook_copy_passes_the_pins():
+    assert not _rook_pin_fails(_mutant_rook("none"))
