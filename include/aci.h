@@ -55,7 +55,16 @@ typedef struct {
 } aci_op;
 
 typedef enum { ACI_TOL_REL = 0, ACI_TOL_ABS = 1 } aci_tol_kind;
-typedef enum { ACI_PIVOT_FULL = 0 } aci_pivot_mode;   /* full search of Algorithm 2 */
+/* Pivot search of Algorithm 2.
+ *  ACI_PIVOT_FULL  argmax over the whole Schur complement at every step (the paper's prrLU).
+ *  ACI_PIVOT_ROOK  rook search (not in the paper; its O(d chi'^3) cost per update in App. A fits a
+ *                  partial search): residual columns and rows R = M - L D U are formed one at a
+ *                  time; from a start column (step 0: the column of max|M|; later the largest
+ *                  residual of the previous pivot row) a row argmax and a column argmax alternate
+ *                  until a fixed point or the fourth hop. O((m + n) p) work per step instead of
+ *                  O(m n); the error estimate is the rejected rook pivot's magnitude. Requires
+ *                  min(m, n, max_rank) <= 4096 (real) / 2048 (complex) per bond. */
+typedef enum { ACI_PIVOT_FULL = 0, ACI_PIVOT_ROOK = 1 } aci_pivot_mode;
 /* Arithmetic of the contractions (the frame half-products of Algorithm 5 and the Pi blocks of
  * Eq. (pifromframes)). The pivot search (Algorithm 2), its Schur updates and error estimates and
  * the output assembly Y = T P^-1 run in FP64 / complex128 in every mode.

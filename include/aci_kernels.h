@@ -66,6 +66,14 @@ aci_status aci_k_prrlu(aci_ctx *ctx, int32_t dtype, const void *Min, int32_t m, 
                        double tau, int32_t chimax, int32_t *piv_rows, int32_t *piv_cols,
                        void *D, void *L, void *U, int32_t *k_out, double *eps_out);
 
+/* aci_k_prrlu with the rook search of ACI_PIVOT_ROOK (aci.h): the same arguments, layouts and
+ * results (the error estimate is the rejected rook pivot's magnitude). L and U may be NULL (the
+ * call then uses scratch for the residual factors). min(m, n, chimax) <= 4096 real / 2048 complex,
+ * else ACI_E_SHAPE. */
+aci_status aci_k_prrlu_rook(aci_ctx *ctx, int32_t dtype, const void *Min, int32_t m, int32_t n,
+                            double tau, int32_t chimax, int32_t *piv_rows, int32_t *piv_cols,
+                            void *D, void *L, void *U, int32_t *k_out, double *eps_out);
+
 /* Random initial guess Y^init (Algorithm 1 input; Sec. 2.6): fills cores[s]
  * (rank[s] x d[s] x rank[s+1]) with SplitMix64 uniforms in [-1, 1): real entry e of the
  * concatenated cores uses counter e, complex entry e uses 2e (re) and 2e+1 (im).

@@ -70,7 +70,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 # Every symbol the headers declare; tests check the library exports each one.
 EXPORTS = ["aci_create", "aci_destroy", "aci_last_error", "aci_opts_default", "aci_elementwise",
            "aci_elementwise_ex", "aci_tt_release", "aci_k_frame_gemm", "aci_k_pi_block",
-           "aci_k_frame_gemm_prec", "aci_k_pi_block_prec", "aci_k_prrlu",
+           "aci_k_frame_gemm_prec", "aci_k_pi_block_prec", "aci_k_prrlu", "aci_k_prrlu_rook",
            "aci_k_tt_random", "aci_k_apply_pinv", "aci_k_prrlu_static", "aci_k_reciprocal"]
 
 _lib = None
@@ -110,6 +110,7 @@ def load_library(build_if_missing: bool = True) -> C.CDLL:
                                         C.POINTER(i32), AciOp, vp, C.POINTER(dbl)]
     lib.aci_k_prrlu.argtypes = [vp, i32, vp, i32, i32, dbl, i32, vp, vp, vp, vp, vp,
                                 C.POINTER(i32), C.POINTER(dbl)]
+    lib.aci_k_prrlu_rook.argtypes = lib.aci_k_prrlu.argtypes
     lib.aci_k_tt_random.argtypes = [vp, i32, C.c_uint64, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(vp)]
     lib.aci_k_apply_pinv.argtypes = [vp, i32, vp, i32, i32, vp, vp, vp, vp]
     lib.aci_k_reciprocal.argtypes = [vp, vp, i32, vp]
@@ -231,7 +232,7 @@ class Context:
     # ------------------------------------------------------------ the method
     def elementwise(self, a, b=None, op="mul", tol=1e-10, max_rank=64, *, tol_kind="rel",
                     max_sweeps=20, seed=0, init=None, coef=None, out_memory="device",
-                    pivots=False, profile=False, precision="fp64"):
+                    pivots=False, profile=False, precision="fp64", pivot_mode="full"):
         """y ~ f(a, b) by ACI. ``a``/``b``: lists of cores (torch CUDA tensors, or numpy arrays
         for host memory). ``precision``: "fp64" or "bf16xS" (S = 2..8 digit planes) for the
         frame and Pi contractions. Returns (cores, stats dict)."""
@@ -246,6 +247,7 @@ class Context:
         opts.out_memory = ACI_MEM_HOST if out_memory == "host" else ACI_MEM_DEVICE
         opts.profile = 1 if profile else 0
         opts.precision = _precision_code(precision)
+        opts.pivot_mode = {"full": 0, "rook": 1}[pivot_mode]
         It = None
         if init is not None:
             It = _TTArg(init)
@@ -328,8 +330,8 @@ class Context:
                                                  C.byref(mx)))
         return Pi, mx.value
 
-    def prrlu(self, M, tau, chimax, with_lu=True):
-        """Algorithm 2 on a device matrix; returns dict(I, J, D, L, U, k, eps)."""
+    def prrlu(self, M, tau, chimax, with_lu=True, mode="full"):
+        """Algorithm 2 on a device matrix (``mode`` "full" or "rook"); returns dict(I, J, D, L, U, k, eps)."""
         import torch
         m, n = M.shape
         kc = min(m, n, chimax)
@@ -340,10 +342,11 @@ class Context:
         Um = torch.zeros((kc, n), dtype=M.dtype, device=M.device) if with_lu else None
         k = C.c_int32()
         eps = C.c_double()
-        self._check(self.lib.aci_k_prrlu(self.handle, _dtype_code(M), M.contiguous().data_ptr(), m, n,
-                                         float(tau), int(chimax), pr.data_ptr(), pc.data_ptr(), D.data_ptr(),
-                                         Lm.data_ptr() if with_lu else None, Um.data_ptr() if with_lu else None,
-                                         C.byref(k), C.byref(eps)))
+        fn = self.lib.aci_k_prrlu_rook if mode == "rook" else self.lib.aci_k_prrlu
+        self._check(fn(self.handle, _dtype_code(M), M.contiguous().data_ptr(), m, n,
+                       float(tau), int(chimax), pr.data_ptr(), pc.data_ptr(), D.data_ptr(),
+                       Lm.data_ptr() if with_lu else None, Um.data_ptr() if with_lu else None,
+                       C.byref(k), C.byref(eps)))
         kk = k.value
         out = dict(I=pr[:kk].cpu().numpy(), J=pc[:kk].cpu().numpy(), D=D[:kk].cpu().numpy(), k=kk,
                    eps=eps.value)

@@ -145,6 +145,7 @@ struct Run {
     cudaStream_t st;
     int L = 0, N = 0, chimax = 0, maxit = 20, rel = 1, prof = 0;
     int digits = 0;            // 0: FP64 contractions; 2..8: BF16 digit planes on the tensor cores
+    int rook = 0;              // pivot search: 0 full, 1 rook
     // per-kernel-class accounting (aci_kernel_class)
     double kms[4] = {0, 0, 0, 0};
     long long kcount[4] = {0, 0, 0, 0};
@@ -309,6 +310,22 @@ struct Run {
         jprev_dev = c.take<int*>(std::max(nb, 1));
     }
 
+    // exchange words and scratch of one pivot search of capacity m x n
+    void size_pivot_search(int m, int n) {
+        if (rook) {
+            const int kc = std::min(std::min(m, n), chimax);
+            if (kc > (is_cplx ? 2048 : 4096)) fail(ctx, ACI_E_SHAPE, "rook search supports at most 4096 (real) / 2048 (complex) pivots per bond");
+            const int G = aci::prrlu_rook_grid(m, n, ctx->num_sms);
+            Gmax = std::max(Gmax, G);
+            ll_words = std::max(ll_words, aci::prrlu_rook_ll_words(G));
+            wcap = std::max(wcap, aci::prrlu_rook_scratch_elems(m, n, is_cplx));
+        } else {
+            const int G = aci::prrlu_grid(m, n, ctx->num_sms);
+            Gmax = std::max(Gmax, G);
+            ll_words = std::max(ll_words, aci::prrlu_ll_words(m, G, is_cplx));
+        }
+    }
+
     void plan_sizes() {
         cap.assign(L + 1, 1);
         const long long big = 1LL << 40;
@@ -342,9 +359,7 @@ struct Run {
             kcap[b] = cap[b + 1];
             wcap = std::max(wcap, (size_t)mcap[b] * ncap[b]);
             mmax_all = std::max(mmax_all, mcap[b]);
-            const int G = aci::prrlu_grid(mcap[b], ncap[b], ctx->num_sms);
-            Gmax = std::max(Gmax, G);
-            ll_words = std::max(ll_words, aci::prrlu_ll_words(mcap[b], G, is_cplx));
+            size_pivot_search(mcap[b], ncap[b]);
             if ((long long)mcap[b] * ncap[b] >= (1LL << 31))
                 fail(ctx, ACI_E_SHAPE, "a Pi block would exceed 2^31 entries");
         }
@@ -373,9 +388,7 @@ struct Run {
             const int m = ry[s], n = d[s] * cap[s + 1];
             wcap = std::max(wcap, (size_t)m * n);
             mmax_all = std::max(mmax_all, m);
-            const int G = aci::prrlu_grid(m, n, ctx->num_sms);
-            Gmax = std::max(Gmax, G);
-            ll_words = std::max(ll_words, aci::prrlu_ll_words(m, G, is_cplx));
+            size_pivot_search(m, n);
         }
     }
 
@@ -427,12 +440,13 @@ struct Run {
         a.piv_rows = prow[b_store];
         a.piv_cols = pcol[b_store];
         a.D = D[b_store];
-        if (with_lu) {
+        if (with_lu || rook) {  // the rook search keeps its factors: they form its residuals
             a.L = Lm[b_store];
             a.Lld = mcap[b_store];
             a.U = Um[b_store];
             a.Uld = ncap[b_store];
         }
+        a.rook = rook;
         a.tol = tol;
         a.rel = rel;
         a.smax = S;
@@ -443,7 +457,7 @@ struct Run {
         a.nmax = nn;
         a.err = err;
         a.flops = flops_of(ACI_KCLASS_PIVOT);
-        const int G = aci::prrlu_grid(mm, nn, ctx->num_sms);
+        const int G = rook ? aci::prrlu_rook_grid(mm, nn, ctx->num_sms) : aci::prrlu_grid(mm, nn, ctx->num_sms);
         cudaEvent_t e = pre(ACI_KCLASS_PIVOT);
         ck(ctx, aci::launch_prrlu<T>(a, G, st), "prrlu launch");
         post(ACI_KCLASS_PIVOT, e, "prrlu");
@@ -887,6 +901,7 @@ aci_status run_typed(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, 
     R.maxit = o.max_sweeps;
     R.prof = o.profile ? 1 : 0;
     R.digits = o.precision;
+    R.rook = o.pivot_mode == ACI_PIVOT_ROOK ? 1 : 0;
     R.seed = o.seed;
     R.op = make_op<T>(op);
     R.init = o.init;
@@ -969,7 +984,7 @@ aci_status aci_elementwise_ex(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, ac
         if (opts) o = *opts;
         if (o.tol_kind != ACI_TOL_REL && o.tol_kind != ACI_TOL_ABS) fail(ctx, ACI_E_ARG, "bad tol_kind");
         if (o.max_sweeps < 1) fail(ctx, ACI_E_ARG, "max_sweeps must be >= 1");
-        if (o.pivot_mode != ACI_PIVOT_FULL) fail(ctx, ACI_E_ARG, "unsupported pivot mode");
+        if (o.pivot_mode != ACI_PIVOT_FULL && o.pivot_mode != ACI_PIVOT_ROOK) fail(ctx, ACI_E_ARG, "unsupported pivot mode");
         if (!valid_precision(o.precision)) fail(ctx, ACI_E_ARG, "unsupported precision");
         if (o.out_memory != ACI_MEM_DEVICE && o.out_memory != ACI_MEM_HOST) fail(ctx, ACI_E_ARG, "bad out_memory");
         validate_tt(ctx, a, "a");
@@ -1208,9 +1223,10 @@ aci_status aci_k_pi_block(aci_ctx* ctx, int32_t dtype, int32_t nprod, const void
     return aci_k_pi_block_prec(ctx, dtype, ACI_PREC_FP64, nprod, A, B, M, N, K, op, Pi, maxabs);
 }
 
-aci_status aci_k_prrlu(aci_ctx* ctx, int32_t dtype, const void* Min, int32_t m, int32_t n, double tau, int32_t chimax,
-                       int32_t* piv_rows, int32_t* piv_cols, void* D, void* L, void* U, int32_t* k_out,
-                       double* eps_out) {
+namespace {
+aci_status k_prrlu(aci_ctx* ctx, int rook, int32_t dtype, const void* Min, int32_t m, int32_t n, double tau,
+                   int32_t chimax, int32_t* piv_rows, int32_t* piv_cols, void* D, void* L, void* U, int32_t* k_out,
+                   double* eps_out) {
     if (!ctx) return ACI_E_ARG;
     ctx->err.clear();
     try {
@@ -1221,18 +1237,27 @@ aci_status aci_k_prrlu(aci_ctx* ctx, int32_t dtype, const void* Min, int32_t m, 
         ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
         const int kcap = std::min(std::min(m, n), chimax);
         if (kcap > 8190) fail(ctx, ACI_E_SHAPE, "more than 8190 pivots requested");
-        const int G = aci::prrlu_grid(m, n, ctx->num_sms);
+        if (rook && kcap > (dtype == ACI_C128 ? 2048 : 4096)) fail(ctx, ACI_E_SHAPE, "too many pivots for the rook search");
+        const int G = rook ? aci::prrlu_rook_grid(m, n, ctx->num_sms) : aci::prrlu_grid(m, n, ctx->num_sms);
         auto go = [&](auto tag) {
             using T = decltype(tag);
-            const size_t nll = aci::prrlu_ll_words(m, G, sizeof(T) == sizeof(cplx));
+            const bool cv = sizeof(T) == sizeof(cplx);
+            const size_t nll = rook ? aci::prrlu_rook_ll_words(G) : aci::prrlu_ll_words(m, G, cv);
+            const size_t nw = rook ? aci::prrlu_rook_scratch_elems(m, n, cv) : (size_t)m * n;
+            const bool own_lu = rook && (!L || !U);  // the rook search needs its factors
             Carver c;
+            T *Ls = nullptr, *Us = nullptr;
             auto lay = [&](Carver& cv, int** kk, double** ee, int** er, int** chi_d, T** W, unsigned long long** ll) {
                 *kk = cv.take<int>(1);
                 *ee = cv.take<double>(1);
                 *er = cv.take<int>(1);
                 *chi_d = cv.take<int>(1);
-                *W = cv.take<T>((size_t)m * n);
+                *W = cv.take<T>(nw);
                 *ll = cv.take<unsigned long long>(nll);
+                if (own_lu) {
+                    Ls = cv.take<T>((size_t)m * kcap);
+                    Us = cv.take<T>((size_t)kcap * n);
+                }
             };
             int *kk, *er, *chi_d;
             double* ee;
@@ -1257,10 +1282,11 @@ aci_status aci_k_prrlu(aci_ctx* ctx, int32_t dtype, const void* Min, int32_t m, 
             a.piv_rows = piv_rows;
             a.piv_cols = piv_cols;
             a.D = static_cast<T*>(D);
-            a.L = static_cast<T*>(L);
+            a.L = own_lu ? Ls : static_cast<T*>(L);
             a.Lld = m;
-            a.U = static_cast<T*>(U);
+            a.U = own_lu ? Us : static_cast<T*>(U);
             a.Uld = n;
+            a.rook = rook;
             a.tol = tau;
             a.rel = 0;
             a.W = W;
@@ -1287,6 +1313,19 @@ aci_status aci_k_prrlu(aci_ctx* ctx, int32_t dtype, const void* Min, int32_t m, 
     } catch (Fail& f) {
         return f.st;
     }
+}
+}  // namespace
+
+aci_status aci_k_prrlu(aci_ctx* ctx, int32_t dtype, const void* Min, int32_t m, int32_t n, double tau, int32_t chimax,
+                       int32_t* piv_rows, int32_t* piv_cols, void* D, void* L, void* U, int32_t* k_out,
+                       double* eps_out) {
+    return k_prrlu(ctx, 0, dtype, Min, m, n, tau, chimax, piv_rows, piv_cols, D, L, U, k_out, eps_out);
+}
+
+aci_status aci_k_prrlu_rook(aci_ctx* ctx, int32_t dtype, const void* Min, int32_t m, int32_t n, double tau,
+                            int32_t chimax, int32_t* piv_rows, int32_t* piv_cols, void* D, void* L, void* U,
+                            int32_t* k_out, double* eps_out) {
+    return k_prrlu(ctx, 1, dtype, Min, m, n, tau, chimax, piv_rows, piv_cols, D, L, U, k_out, eps_out);
 }
 
 aci_status aci_k_tt_random(aci_ctx* ctx, int32_t dtype, uint64_t seed, int32_t L, const int32_t* d,

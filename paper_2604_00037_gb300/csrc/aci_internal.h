@@ -96,6 +96,7 @@ template <class T> struct PrrluArgs {
     unsigned int tagbase;    // tags are tagbase + step + 1; distinct per launch since the area was cleared
     int mmax, nmax;     // capacities of this launch
     int* err;           // device error flags (DevErr)
+    int rook;           // 1: rook search (W holds prrlu_rook_scratch_elems, ll prrlu_rook_ll_words(G); L, U required)
     // filled by launch_prrlu
     int epc, wcap_elems, wcap_cols;
 };
@@ -108,6 +109,9 @@ constexpr unsigned int kPrrluMaxLaunches = (1u << (32 - kPrrluStepBits)) - 1;
 
 template <class T> cudaError_t launch_prrlu(const PrrluArgs<T>& a, int G, cudaStream_t st);
 int prrlu_grid(int mmax, int nmax, int num_sms);
+int prrlu_rook_grid(int mmax, int nmax, int num_sms);
+size_t prrlu_rook_ll_words(int G);
+size_t prrlu_rook_scratch_elems(int mmax, int nmax, bool cplx_values);
 size_t prrlu_ll_words(int mmax, int G, bool cplx_values);
 // y[i] = 1 / x[i] with the reciprocal the pivot search uses (step-level entry point).
 void launch_recip(const double* x, int n, double* y, cudaStream_t st);

@@ -861,6 +861,379 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
     cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
+// ---------------------------------------------------------------- rook search (second pivot mode)
+//
+// The rook variant of Algorithm 2's pivot search. The residual
+//   R_p = M - sum_{q<p} L[:, q] D[q] U[q, :]
+// is never formed as a whole: each hop evaluates one column (or row) of it, a matrix-vector
+// product with the stored factors, and takes its argmax over the unused rows (columns). From the
+// start column c0: r1 = argmax_r |R(r,c0)|, c1 = argmax_c |R(r1,c)|; c1 == c0 accepts (r1, c0);
+// else r2 = argmax_r |R(r,c1)|; r2 == r1 accepts (r1, c1), otherwise (r2, c1) after a fourth hop
+// (the row r2 is evaluated for U). Step 0 starts from the column of the global argmax of |M|,
+// step p from the largest residual of the previous pivot row among unused columns. Work per
+// step is O((m + n) p) instead of the O(m n) Schur update of the full search.
+//
+// One persistent cooperative grid. A hop's evaluation splits the rows (columns) into blocks of
+// RKB, each handled by one CTA with RKQ partial sums per row (q strided), so L (column-major) and
+// U (row-major) are read coalesced; a CTA owns the same rows and columns at every step, writes
+// their L and U entries and keeps their used flags, so nothing it reads from L or U was written
+// by another CTA except the pivot row of L and the start column of U, which are read after an
+// exchange (or, for the newest U row, re-derived from the previous step's residual row). Each
+// hop ends in a grid-wide (key, index) argmax: every CTA publishes its best (two best for rows:
+// the second gives the next start column) as tagged words and gathers all records (bounded waits).
+constexpr int RKT = 256;          // threads per CTA
+constexpr int RKB = 16;           // rows (columns) per evaluation block
+constexpr int RKQ = RKT / RKB;    // partial sums per row, q = j, j + RKQ, ...
+constexpr int RK_REC = 16;        // words per record (one 128-byte line): ready tag, key, index, key2, index2, value
+constexpr int RK_AREAS = 5;       // global argmax, column, row, second column, second row
+
+// The two best (key, index) pairs seen, with the best one's value.
+template <class T> struct RkCand {
+    kbits_t k1;
+    int i1;
+    kbits_t k2;
+    int i2;
+    T v1;
+};
+
+template <class T>
+__device__ __forceinline__ void rk_push(kbits_t k, int i, T v, RkCand<T>& c) {
+    if (i == INT_MAX) return;
+    if (better(k, i, c.k1, c.i1)) {
+        c.k2 = c.k1;
+        c.i2 = c.i1;
+        c.k1 = k;
+        c.i1 = i;
+        c.v1 = v;
+    } else if (better(k, i, c.k2, c.i2)) {
+        c.k2 = k;
+        c.i2 = i;
+    }
+}
+template <class T> __device__ __forceinline__ RkCand<T> rk_none() {
+    return RkCand<T>{0ull, INT_MAX, 0ull, INT_MAX, s_zero(T())};
+}
+__device__ __forceinline__ double shfl_val(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ cplx shfl_val(cplx v, int off) {
+    return mkc(__shfl_xor_sync(0xffffffffu, v.re, off), __shfl_xor_sync(0xffffffffu, v.im, off));
+}
+template <class T> __device__ __forceinline__ void rk_warp_merge(RkCand<T>& c) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const kbits_t k1 = __shfl_xor_sync(0xffffffffu, c.k1, off);
+        const int i1 = __shfl_xor_sync(0xffffffffu, c.i1, off);
+        const kbits_t k2 = __shfl_xor_sync(0xffffffffu, c.k2, off);
+        const int i2 = __shfl_xor_sync(0xffffffffu, c.i2, off);
+        const T v1 = shfl_val(c.v1, off);
+        rk_push(k1, i1, v1, c);
+        rk_push(k2, i2, s_zero(T()), c);
+    }
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void rk_put_val(unsigned long long* p, double v) {
+    st_relaxed_u64(p, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void rk_put_val(unsigned long long* p, cplx v) {
+    st_relaxed_u64(p, (unsigned long long)__double_as_longlong(v.re));
+    st_relaxed_u64(p + 1, (unsigned long long)__double_as_longlong(v.im));
+}
+__device__ __forceinline__ void rk_get_val(const unsigned long long* p, double& v) { v = __longlong_as_double((long long)ld_word(p)); }
+__device__ __forceinline__ void rk_get_val(const unsigned long long* p, cplx& v) {
+    v = mkc(__longlong_as_double((long long)ld_word(p)), __longlong_as_double((long long)ld_word(p + 1)));
+}
+
+// Publish this CTA's candidates under `tag`, then gather every CTA's record: the grid's two best
+// with the best one's value, returned to every thread. A record is one 128-byte line: the data
+// words, then a ready word holding the tag, stored with release semantics after a fence that
+// orders the CTA's earlier global writes (residual buffers, L, U; the barrier before it collects
+// them from every thread). Warp 0 polls only the ready words (acquire loads), reads each record
+// once, and the closing barrier passes the acquired view to the whole CTA. false: a wait ran out.
+template <class T>
+__device__ bool rk_exchange(unsigned long long* area, unsigned int tag, RkCand<T> mine, RkCand<T>& out,
+                            RkCand<T>* s, int* sok) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    rk_warp_merge(mine);
+    if (lane == 0) s[warp] = mine;
+    __syncthreads();
+    if (warp == 0) {
+        RkCand<T> c = lane < RKT / 32 ? s[lane] : rk_none<T>();
+        rk_warp_merge(c);
+        if (lane == 0) {
+            unsigned long long* rec = area + (size_t)blockIdx.x * RK_REC;
+            fence_acq_rel_gpu();
+            st_relaxed_u64(rec + 1, c.k1);
+            st_relaxed_u64(rec + 2, (unsigned long long)(unsigned int)c.i1);
+            st_relaxed_u64(rec + 3, c.k2);
+            st_relaxed_u64(rec + 4, (unsigned long long)(unsigned int)c.i2);
+            rk_put_val(rec + 5, c.v1);
+            st_release_u64(rec, tag);
+        }
+    }
+    // every thread gathers records t, t + RKT, ... (one round trip for the ready word, one for the data)
+    RkCand<T> g = rk_none<T>();
+    bool ok = true;
+    for (int t = threadIdx.x; t < (int)gridDim.x && ok; t += RKT) {
+        const unsigned long long* rec = area + (size_t)t * RK_REC;
+        long long spins = 0;
+        while (ld_word(rec) != (unsigned long long)tag) {  // relaxed polling; one acquire fence after
+            if (++spins > kSpinLimit) {
+                ok = false;
+                break;
+            }
+        }
+        if (!ok) break;
+        fence_acq_rel_gpu();
+        T v;
+        rk_get_val(rec + 5, v);
+        rk_push(ld_word(rec + 1), (int)(unsigned int)ld_word(rec + 2), v, g);
+        rk_push(ld_word(rec + 3), (int)(unsigned int)ld_word(rec + 4), s_zero(T()), g);
+    }
+    ok = __syncthreads_and(ok);
+    rk_warp_merge(g);
+    if (lane == 0) s[warp] = g;
+    __syncthreads();
+    if (warp == 0) {
+        g = lane < RKT / 32 ? s[lane] : rk_none<T>();
+        rk_warp_merge(g);
+        if (lane == 0) {
+            s[RKT / 32] = g;
+            *sok = ok;
+        }
+    }
+    __syncthreads();
+    out = s[RKT / 32];
+    return *sok != 0;
+}
+
+__device__ __forceinline__ double rk_sub(double a, double b) { return a - b; }
+__device__ __forceinline__ cplx rk_sub(cplx a, cplx b) { return mkc(a.re - b.re, a.im - b.im); }
+
+// Residual column c over this CTA's rows: buf[r] = M[r, c] - sum_{q<p} L[r, q] w[q]; the CTA's
+// best unused row. (Row evaluation is the same with the roles of the factors exchanged.)
+template <class T, bool COL>
+__device__ RkCand<T> rk_eval(const PrrluArgs<T>& a, const unsigned char* used, int len, int ldm, int fixed, int p,
+                             const T* w, T* part, T* buf) {
+    RkCand<T> best = rk_none<T>();
+    const int j = threadIdx.x % RKB, qc = threadIdx.x / RKB;
+    for (int blk = blockIdx.x; blk * RKB < len; blk += gridDim.x) {
+        const int x = blk * RKB + j;  // the row (COL) or column (row evaluation)
+        T acc = s_zero(T());
+        if (x < len) {
+            if (COL) {
+#pragma unroll 4
+                for (int q = qc; q < p; q += RKQ) acc = s_fma(a.L[(size_t)q * a.Lld + x], w[q], acc);
+            } else {
+#pragma unroll 4
+                for (int q = qc; q < p; q += RKQ) acc = s_fma(w[q], a.U[(size_t)q * a.Uld + x], acc);
+            }
+        }
+        part[threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x < RKB && x < len) {
+            T sum = part[threadIdx.x];
+            for (int t = 1; t < RKQ; ++t) sum = s_add(sum, part[threadIdx.x + t * RKB]);
+            const T mv = COL ? a.Min[(size_t)x * ldm + fixed] : a.Min[(size_t)fixed * ldm + x];
+            const T R = rk_sub(mv, sum);
+            buf[x] = R;
+            if (!used[x]) rk_push(key_of(R), x, R, best);
+        }
+        __syncthreads();
+    }
+    return best;
+}
+
+template <class T>
+__global__ void __launch_bounds__(RKT, 1) prrlu_rook_kernel(PrrluArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char rk_smem[];
+    const int kcap_s = a.wcap_cols;  // shared capacity of the pivot and weight vectors
+    T* Ds = reinterpret_cast<T*>(rk_smem);
+    T* w = Ds + kcap_s;
+    T* part = w + kcap_s;
+    RkCand<T>* sc = align16<RkCand<T>>(part + RKT);
+    Decision<T>* dec = align16<Decision<T>>(sc + RKT / 32 + 1);
+    int* sok = reinterpret_cast<int*>(dec + 1);
+    const int m = dimv(a.m, a.chi), n = dimv(a.n, a.chi);
+    const int ldm = n;
+    const int kmin = m < n ? m : n;
+    const double S = a.rel ? __longlong_as_double((long long)*a.smax) : 0.0;
+    const double tau = a.rel ? a.tol * S : a.tol;
+    // scratch: two residual columns, two residual rows, used flags (see prrlu_rook_scratch_bytes)
+    T* colbuf[2] = {a.W, a.W + a.mmax};
+    T* rowbuf[2] = {a.W + 2 * (size_t)a.mmax, a.W + 2 * (size_t)a.mmax + a.nmax};
+    unsigned char* used_r = reinterpret_cast<unsigned char*>(a.W + 2 * (size_t)a.mmax + 2 * (size_t)a.nmax);
+    unsigned char* used_c = used_r + a.mmax;
+    unsigned long long* area[RK_AREAS];
+    for (int i = 0; i < RK_AREAS; ++i) area[i] = a.ll + (size_t)i * gridDim.x * RK_REC;
+    const double per = sizeof(T) == sizeof(cplx) ? 8.0 : 2.0;
+    double flops = 0.0;
+
+    for (int blk = blockIdx.x; blk * RKB < m; blk += gridDim.x)
+        if (threadIdx.x < RKB && blk * RKB + (int)threadIdx.x < m) used_r[blk * RKB + threadIdx.x] = 0;
+    for (int blk = blockIdx.x; blk * RKB < n; blk += gridDim.x)
+        if (threadIdx.x < RKB && blk * RKB + (int)threadIdx.x < n) used_c[blk * RKB + threadIdx.x] = 0;
+
+    int p = 0, c0 = 0, prev_row = 0;
+    T prev_inv = s_zero(T());
+    int prev_zero = 0;
+    int code = 1;
+    double eps = 0.0;
+    bool ok = true;
+    for (;; ++p) {
+        if (p == kmin) {
+            code = 1;
+            eps = 0.0;
+            break;
+        }
+        const unsigned int tag = a.tagbase + (unsigned int)p + 1;
+        RkCand<T> g;
+        if (p == 0) {  // start column: the column of the global argmax of |M| (ties: lowest row * n + col)
+            RkCand<T> mine = rk_none<T>();
+            const long long mn = (long long)m * n;
+            for (long long e = (long long)blockIdx.x * RKT + threadIdx.x; e < mn; e += (long long)gridDim.x * RKT)
+                rk_push(key_of(a.Min[e]), (int)e, s_zero(T()), mine);
+            if (!(ok = rk_exchange(area[0], tag, mine, g, sc, sok))) break;
+            c0 = g.i1 == INT_MAX ? 0 : g.i1 % n;
+        }
+        // weights of the start column: w[q] = D[q] U[q, c0]; the newest U row comes from the previous
+        // step's residual row with the arithmetic its writers used
+        for (int q = threadIdx.x; q < p; q += RKT) {
+            T u;
+            if (q < p - 1) {
+                u = ldcg_val(a.U + (size_t)q * a.Uld + c0);
+            } else {
+                u = prev_zero ? s_zero(T()) : s_mul(ldcg_val(rowbuf[prev_row] + c0), prev_inv);
+            }
+            w[q] = s_mul(Ds[q], u);
+        }
+        __syncthreads();
+        // hop 1: column c0
+        RkCand<T> best = rk_eval<T, true>(a, used_r, m, ldm, c0, p, w, part, colbuf[0]);
+        flops += per * m * (double)p;
+        if (!(ok = rk_exchange(area[1], tag, best, g, sc, sok))) break;
+        const int r1 = g.i1;
+        T pv = g.v1;  // residual at (r1, c0): the pivot if the search stops here
+        // hop 2: row r1
+        for (int q = threadIdx.x; q < p; q += RKT) w[q] = s_mul(ldcg_val(a.L + (size_t)q * a.Lld + r1), Ds[q]);
+        __syncthreads();
+        best = rk_eval<T, false>(a, used_c, n, ldm, r1, p, w, part, rowbuf[0]);
+        flops += per * n * (double)p;
+        RkCand<T> row1;
+        if (!(ok = rk_exchange(area[2], tag, best, row1, sc, sok))) break;
+        int r = r1, c = c0, ci = 0, ri = 0;
+        RkCand<T> rowsel = row1;
+        if (row1.i1 != c0) {
+            const int c1 = row1.i1;
+            // hop 3: column c1 (every U row it needs has been published by now)
+            for (int q = threadIdx.x; q < p; q += RKT)
+                w[q] = s_mul(Ds[q], ldcg_val(a.U + (size_t)q * a.Uld + c1));
+            __syncthreads();
+            best = rk_eval<T, true>(a, used_r, m, ldm, c1, p, w, part, colbuf[1]);
+            flops += per * m * (double)p;
+            if (!(ok = rk_exchange(area[3], tag, best, g, sc, sok))) break;
+            const int r2 = g.i1;
+            pv = g.v1;  // the pivot lies in column c1, at r2 (== r1 at a fixed point)
+            c = c1;
+            ci = 1;
+            if (r2 != r1) {
+                // hop 4: row r2, for the pivot's U row
+                for (int q = threadIdx.x; q < p; q += RKT)
+                    w[q] = s_mul(ldcg_val(a.L + (size_t)q * a.Lld + r2), Ds[q]);
+                __syncthreads();
+                best = rk_eval<T, false>(a, used_c, n, ldm, r2, p, w, part, rowbuf[1]);
+                flops += per * n * (double)p;
+                if (!(ok = rk_exchange(area[4], tag, best, rowsel, sc, sok))) break;
+                r = r2;
+                ri = 1;
+            }
+        }
+        // the pivot and the stop test (Algorithm 2, reading R2 with the rook pivot)
+        if (threadIdx.x == 0) {
+            decide(dec, key_of(pv), r, pv, p, a.chimax, tau);
+            dec->piv = pv;
+        }
+        __syncthreads();
+        if (dec->code != 0) {
+            code = dec->code;
+            eps = dec->eps;
+            break;
+        }
+        const T piv = dec->piv, inv = dec->inv;
+        const int zp = dec->zpiv;
+        // L column p over this CTA's rows, U row p over its columns; zero on used rows / columns
+        for (int blk = blockIdx.x; blk * RKB < m; blk += gridDim.x) {
+            const int x = blk * RKB + (int)threadIdx.x;
+            if (threadIdx.x < RKB && x < m) {
+                T l;
+                if (x == r) l = s_one(T());
+                else if (zp || used_r[x]) l = s_zero(T());
+                else l = s_mul(colbuf[ci][x], inv);
+                a.L[(size_t)p * a.Lld + x] = l;
+                if (x == r) used_r[x] = 1;
+            }
+        }
+        for (int blk = blockIdx.x; blk * RKB < n; blk += gridDim.x) {
+            const int x = blk * RKB + (int)threadIdx.x;
+            if (threadIdx.x < RKB && x < n) {
+                T u;
+                if (x == c) u = s_one(T());
+                else if (zp || used_c[x]) u = s_zero(T());
+                else u = s_mul(rowbuf[ri][x], inv);
+                a.U[(size_t)p * a.Uld + x] = u;
+                if (x == c) used_c[x] = 1;
+            }
+        }
+        if (threadIdx.x == 0) {
+            Ds[p] = piv;
+            if (blockIdx.x == 0) {
+                a.D[p] = piv;
+                a.piv_rows[p] = r;
+                a.piv_cols[p] = c;
+            }
+        }
+        // next start column: the largest residual of this pivot row among the unused columns
+        c0 = rowsel.i1 != c ? rowsel.i1 : rowsel.i2;
+        if (c0 == INT_MAX) c0 = 0;  // no unused column left: the next step stops at p == min(m, n)
+        prev_row = ri;
+        prev_inv = inv;
+        prev_zero = zp;
+        __syncthreads();
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(a.err, DEVERR_TIMEOUT);
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (code == 2) atomicOr(a.err, DEVERR_NUMERIC);
+        *a.eps_out = eps;
+        if (a.k_out) *a.k_out = p;
+        if (a.out_chi_idx >= 0) const_cast<int*>(a.chi)[a.out_chi_idx] = p;
+        if (a.flops) atomicAdd(a.flops, flops);
+    }
+}
+
+template <class T>
+size_t rook_smem_bytes(int kcap) {
+    size_t b = sizeof(T) * (2 * (size_t)kcap + RKT);
+    b = (b + 15) & ~(size_t)15;
+    b += sizeof(RkCand<T>) * (RKT / 32 + 1);
+    b = (b + 15) & ~(size_t)15;
+    b += sizeof(Decision<T>) + 16;
+    return b;
+}
+
 template <class T>
 size_t creg_bytes(int mmax, int C, int wmax) {
     size_t b = sizeof(T) * (2 * (size_t)mmax + wmax);
@@ -895,6 +1268,18 @@ int prrlu_epc() {
 
 int prrlu_grid(int mmax, int nmax, int num_sms) {
     return live_ctas((long long)mmax * nmax, nmax, std::min(num_sms, PT), prrlu_epc());
+}
+
+int prrlu_rook_grid(int mmax, int nmax, int num_sms) {
+    const int blocks = std::max((mmax + RKB - 1) / RKB, (nmax + RKB - 1) / RKB);
+    return std::max(1, std::min(blocks, num_sms));
+}
+
+size_t prrlu_rook_ll_words(int G) { return (size_t)RK_AREAS * G * RK_REC; }
+
+size_t prrlu_rook_scratch_elems(int mmax, int nmax, bool cplx_values) {
+    const size_t vb = cplx_values ? 16 : 8;
+    return 2 * (size_t)mmax + 2 * (size_t)nmax + ((size_t)mmax + nmax + vb - 1) / vb;
 }
 
 size_t prrlu_ll_words(int mmax, int G, bool cplx_values) {
@@ -961,6 +1346,27 @@ template <class T>
 cudaError_t launch_prrlu(const PrrluArgs<T>& a_in, int G, cudaStream_t st) {
     PrrluArgs<T> a = a_in;
     const bool cp = sizeof(T) == sizeof(cplx);
+    if (a.rook) {
+        // the caller sized W (prrlu_rook_scratch_elems), ll (prrlu_rook_ll_words(G)) and gives L, U
+        const int kcap = std::max(1, std::min(std::min(a.mmax, a.nmax), a.chimax));
+        const size_t smem = rook_smem_bytes<T>(kcap);
+        if (smem > kSmemLimit || !a.L || !a.U) return cudaErrorInvalidValue;
+        a.wcap_cols = kcap;
+        auto fn = prrlu_rook_kernel<T>;
+        cudaError_t e = kernel_attrs((const void*)fn);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(G);
+        cfg.blockDim = dim3(RKT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, fn, a);
+    }
     const long long work = (long long)a.mmax * a.nmax * (cp ? 4 : 1);
     if (work <= kClusterWorkMax) {
         const int cmax = max_cluster<T>();
