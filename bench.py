@@ -11,7 +11,10 @@ Prints one JSON line (rank 0). `value` = products per second over all ranks. The
 flushed (a 256 MB write, outside the timed events) before every timed step. The `roofline`
 object is for the kernel class with the largest share of device time, from CUDA events recorded
 by the library on its stream around every launch during the timed steps. `cpu_baseline` times
-the CPU oracle on a bounded sample of the same workload on this host.
+the CPU oracle on a bounded sample of the same workload on this host. `mixed` repeats the
+workload with the frame and Pi contractions on the tensor cores (BF16 digit planes, --mixed-digits
+of them) and states its sampled error against the exact product and against the FP64 result, with
+a tensor-pipe roofline for those contractions.
 """
 
 import argparse
@@ -44,7 +47,17 @@ def parse():
     ap.add_argument("--chi", type=int, default=128)
     ap.add_argument("--max-sweeps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mixed-digits", type=int, default=6, help="BF16 digit planes of the mixed run (0: skip it)")
     return ap.parse_args()
+
+
+def measured_peak(key, fallback):
+    """A peak from the measured MEASURED_PEAKS.json, else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), "measured"
+    except (OSError, KeyError, ValueError):
+        return fallback, "fallback"
 
 
 def workload(chi):
@@ -281,6 +294,48 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_value = world * len(e2e_t) / float(t.item())
 
+    # the same workload with the contractions on the tensor cores; errors on 20000 sampled points
+    mixed = None
+    if args.mixed_digits:
+        from synthetic.tt import tt_eval
+        prec = f"bf16x{args.mixed_digits}"
+        rng = np.random.default_rng(8)
+        pts = rng.integers(0, 2, size=(20000, len(a)))
+        exact = tt_eval(a, pts) * tt_eval(b, pts)
+        y64 = tt_eval([c.cpu().numpy() for c in y], pts)
+
+        def mstep(profile):
+            return ctx.elementwise(A, B, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps, profile=profile,
+                                   precision=prec)
+        mstep(False)
+        mt, minfo = [], []
+        for k in range(args.steps):
+            flush.fill_((k + 3) & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ym, info = mstep(True)
+            e1.record(stream)
+            e1.synchronize()
+            mt.append(e0.elapsed_time(e1))
+            minfo.append(info)
+        yv = tt_eval([c.cpu().numpy() for c in ym], pts)
+        scale = np.abs(exact).max()
+        tms = sum(i["kernels"][c]["ms"] for i in minfo for c in ("frame", "pi"))
+        tfl = sum(i["kernels"][c]["tensor_flops"] for i in minfo for c in ("frame", "pi"))
+        peak, src = measured_peak("bf16_tflops", 1900.0)
+        ach = tfl / (tms / 1e3) / 1e12
+        mixed = {"precision": prec, "value": world * args.steps / (sum(mt) / 1e3), "unit": UNIT,
+                 "ms_per_step": sum(mt) / args.steps,
+                 "rel_err_vs_exact": float(np.abs(yv - exact).max() / scale),
+                 "rel_err_vs_fp64": float(np.abs(yv - y64).max() / scale),
+                 "fp64_rel_err_vs_exact": float(np.abs(y64 - exact).max() / scale),
+                 "classes_ms_per_step": {c: sum(i["kernels"][c]["ms"] for i in minfo) / args.steps for c in classes},
+                 "roofline_tensor": {"bound": "tensor", "kernel": "tc_split_kernel + tc_gemm_kernel (frames and Pi)",
+                                     "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                                     "peak_source": f"bf16 dense, {src} (burst)",
+                                     "note": "BF16 MMA flops issued / device time of the contraction launches"}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         per, t = oracle_sample(p, args.max_sweeps)
@@ -296,7 +351,7 @@ def main():
                 "config": config_dict(args, p),
                 "result": {"iterations": last["iterations"], "converged": last["converged"],
                            "max_rank": max(last["ranks"]), "max_eps_rel": last["max_eps"] / last["scale"]},
-                "roofline": roofline, "cpu_baseline": cpu,
+                "roofline": roofline, "cpu_baseline": cpu, "mixed": mixed,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
                 "clocks": clk}

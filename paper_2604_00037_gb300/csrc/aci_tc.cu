@@ -43,7 +43,7 @@ namespace {
 
 constexpr int kTileM = 128;                  // rows per output tile (tcgen05 M)
 constexpr int kSlabK = 16;                   // K per slab (tcgen05 K for 16-bit inputs)
-constexpr int kStageSlabs = 2;               // slabs per pipeline stage
+constexpr int kStageSlabs = 1;               // slabs per pipeline stage
 constexpr uint32_t kSlabBytesA = kTileM * kSlabK * 2;  // 4 KB
 constexpr int kSplitMaxWarps = 16;  // warps of a split CTA along K (32 rows per CTA)
 constexpr int kSplitCache = 2;     // 8-wide K groups a lane keeps in registers between the passes
@@ -270,7 +270,7 @@ __device__ __forceinline__ double ldexp_int(long long v, int E) {
 }
 
 template <class T, int NT>
-__global__ void __launch_bounds__(kGemmThreads, 1) tc_gemm_kernel(TcArgs<T> a) {
+__global__ void __launch_bounds__(kGemmThreads, 2) tc_gemm_kernel(TcArgs<T> a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr int cmul = (sizeof(T) == sizeof(cplx)) ? 2 : 1;
     const int S = a.S, nst = a.nst;
@@ -547,13 +547,20 @@ TcPlan tc_plan(int digits, bool cplx_values, int Mmax, int Nmax, int Kmax, int n
     p.bytesB = align256(np * digits * p.ntiles * p.ksl * slabB);
     p.bytesE = align256(sizeof(int) * np * ((size_t)p.mtiles * kTileM + (size_t)p.ntiles * p.NT));
     const size_t stage = (size_t)std::max(digits, 1) * kStageSlabs * (kSlabBytesA + slabB);  // A and B slabs
-    const size_t budget = 200 * 1024;
-    p.nst = (int)std::min<size_t>(4, budget / stage);
-    p.smem = (size_t)p.nst * stage + 8 * (2 * p.nst + 1) + 16 + sizeof(int) * 2 * 64;  // + column scales
-    if (p.smem < 120 * 1024) p.smem = 120 * 1024;  // one CTA per SM: its tensor memory is never contended
     uint32_t cols = 32;
     while (cols < (uint32_t)(p.nacc * digits * p.NT)) cols <<= 1;
     p.tmem_cols = cols;
+    const size_t extra = 8 * (2 * 8 + 1) + 16 + sizeof(int) * 2 * 64;  // barriers, flags, column scales
+    if (cols <= 256) {
+        // two CTAs per SM (their tensor memory fits side by side): one's epilogue overlaps the
+        // other's copies and MMAs; registers (<= 128 per thread) allow no third
+        p.nst = (int)std::min<size_t>(4, (100 * 1024 - extra) / stage);
+        p.smem = (size_t)p.nst * stage + extra;
+    } else {
+        // one CTA per SM: the shared-memory request keeps a second CTA (and its allocation) away
+        p.nst = (int)std::min<size_t>(8, (200 * 1024 - extra) / stage);
+        p.smem = std::max<size_t>((size_t)p.nst * stage + extra, 120 * 1024);
+    }
     p.ok = digits >= kTcMinDigits && digits <= kTcMaxDigits && p.nst >= 1 && cols <= 512 && p.bits >= 3 &&
            digits * p.NT <= 256;
     return p;
