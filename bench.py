@@ -48,7 +48,61 @@ def parse():
     ap.add_argument("--max-sweeps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mixed-digits", type=int, default=6, help="BF16 digit planes of the mixed run (0: skip it)")
+    ap.add_argument("--precision", default="fp64", help="contractions of the headline run: fp64 or bf16xS")
+    ap.add_argument("--pivot-mode", default="full", choices=["full", "rook"])
+    ap.add_argument("--kernel", default="", choices=["", "pi_block", "frame_gemm", "prrlu"],
+                    help="time one step-level call of this shape instead of the product (kernel profiling)")
+    ap.add_argument("--m", type=int, default=2048)
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--k", type=int, default=256)
+    ap.add_argument("--complex", action="store_true")
     return ap.parse_args()
+
+
+def run_kernel(args):
+    """One step-level call, repeated: the Pi block f = |a|^2 a (m x n, K = k), a frame product
+    (m x k times k x n) or the pivot search (m x n, k pivots) on seeded Gaussian inputs."""
+    import numpy as np
+    import torch
+    from paper_2604_00037_gb300.binding import Context
+    ctx = Context(0)
+    rng = np.random.default_rng(0)
+
+    def mat(r, c):
+        x = rng.standard_normal((r, c))
+        if args.complex:
+            x = x + 1j * rng.standard_normal((r, c))
+        return torch.from_numpy(x).cuda()
+    if args.kernel == "pi_block":
+        A, B = mat(args.m, args.k), mat(args.k, args.n)
+        call = lambda: ctx.pi_block([A], [B], "abs2_mul", precision=args.precision)
+        flops = (8.0 if args.complex else 2.0) * args.m * args.n * args.k
+    elif args.kernel == "frame_gemm":
+        A, B = mat(args.m, args.k), mat(args.k, args.n)
+        call = lambda: ctx.frame_gemm(A, B, precision=args.precision)
+        flops = (8.0 if args.complex else 2.0) * args.m * args.n * args.k
+    else:
+        r = min(args.m, args.n, 300)
+        M = (mat(args.m, r) @ mat(r, args.n)).contiguous()
+        call = lambda: ctx.prrlu(M, 0.0, args.k, mode=args.pivot_mode)
+        flops = None
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"kernel": args.kernel, "m": args.m, "n": args.n, "k": args.k, "complex": args.complex,
+            "precision": args.precision, "pivot_mode": args.pivot_mode, "ms_per_call": ms,
+            "note": "per call including the host synchronisation of the step-level entry"}
+    if flops:
+        line["fp64_equivalent_tflops"] = flops / (ms / 1e3) / 1e12
+    print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 def measured_peak(key, fallback):
@@ -71,6 +125,7 @@ def config_dict(args, p):
                         f"a*b, tol {p['tol']:g} rel, max_rank {p['max_rank']}, <= {args.max_sweeps} sweeps",
             "L": 40, "d": 2, "chi": args.chi, "max_rank": p["max_rank"], "tol": p["tol"],
             "op": "a*b", "max_sweeps": args.max_sweeps,
+            "contractions": args.precision, "pivot_search": args.pivot_mode,
             "l2": "flushed before every timed step (256 MB write, untimed)",
             "parallelism": f"replicas x{args.gpus}"}
 
@@ -198,6 +253,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel:
+        return run_kernel(args)
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -219,7 +276,8 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step(profile):
-        return ctx.elementwise(A, B, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps, profile=profile)
+        return ctx.elementwise(A, B, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps, profile=profile,
+                               precision=args.precision, pivot_mode=args.pivot_mode)
 
     for w in range(args.warmup):
         flush.fill_(w & 0xFF)
@@ -347,8 +405,9 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": config_dict(args, p),
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else f"f64 ({args.precision} contractions)",
+                "data": "synthetic", "config": config_dict(args, p),
                 "result": {"iterations": last["iterations"], "converged": last["converged"],
                            "max_rank": max(last["ranks"]), "max_eps_rel": last["max_eps"] / last["scale"]},
                 "roofline": roofline, "cpu_baseline": cpu, "mixed": mixed,
