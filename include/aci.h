@@ -110,6 +110,9 @@ typedef struct {
     int32_t out_memory;    /* aci_memory of the output cores (default device)              */
     int32_t profile;       /* 1: time every kernel with CUDA events on the context stream and
                               count its algorithmic flops (aci_stats.kernel_*); 0: off        */
+    int32_t batch_streams; /* aci_elementwise_batch: products in flight at once (0 = one per 16
+                              SMs, the width of the pivot search's thread-block cluster)       */
+    int32_t _pad2;
 } aci_opts;
 
 /* Kernel classes of aci_stats.kernel_* (profile = 1). Flops are real-equivalent (a complex
@@ -187,6 +190,25 @@ aci_status aci_elementwise(aci_ctx *ctx, const aci_tt *a, const aci_tt *b, aci_o
 aci_status aci_elementwise_ex(aci_ctx *ctx, const aci_tt *a, const aci_tt *b, aci_op op,
                               double tol, int32_t max_rank, const aci_opts *opts,
                               aci_tt *out, aci_stats *stats);
+
+/* Independent products in one call (no counterpart in the paper: a throughput form of
+ * aci_elementwise_ex for many pairs of uneven length and rank). Product i is
+ * f(a[i], b[i]) with op[i], tol[i], max_rank[i] and the shared opts (opts->init must be NULL),
+ * exactly as aci_elementwise_ex would compute it: same kernels, same results bit for bit.
+ * Up to opts->batch_streams products run at once, each on a worker stream of the context with its
+ * own scratch and CUDA graphs, driven by a host thread; workers take the next product as they
+ * finish, so uneven products balance. The pivot search of one product keeps at most one thread-
+ * block cluster (16 SMs) busy, so concurrent products fill the GPU.
+ *  a, out        arrays of n; b an array of n (NULL if every op is ACI_OP_ABS2_MUL);
+ *  op, tol, max_rank  arrays of n; stats (array of n) and status (array of n) may be NULL.
+ * Outputs are owned as for aci_elementwise_ex: release each with aci_tt_release(ctx, &out[i]).
+ * The work is ordered after the context stream's earlier work, and the context stream waits for
+ * it; the call returns when every product is done. Returns ACI_OK, else the first error (its
+ * message in aci_last_error) or a warning; status[i] holds each product's own status. */
+aci_status aci_elementwise_batch(aci_ctx *ctx, int32_t n, const aci_tt *a, const aci_tt *b,
+                                 const aci_op *op, const double *tol, const int32_t *max_rank,
+                                 const aci_opts *opts, aci_tt *out, aci_stats *stats,
+                                 aci_status *status);
 
 /* Free the library-owned parts of an output TT and zero the struct. */
 aci_status aci_tt_release(aci_ctx *ctx, aci_tt *out);

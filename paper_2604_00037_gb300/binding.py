@@ -38,7 +38,8 @@ class AciTT(C.Structure):
 class AciOpts(C.Structure):
     _fields_ = [("tol_kind", C.c_int32), ("max_sweeps", C.c_int32), ("pivot_mode", C.c_int32),
                 ("precision", C.c_int32), ("seed", C.c_uint64), ("init", C.POINTER(AciTT)),
-                ("out_memory", C.c_int32), ("profile", C.c_int32)]
+                ("out_memory", C.c_int32), ("profile", C.c_int32), ("batch_streams", C.c_int32),
+                ("_pad2", C.c_int32)]
 
 
 class AciStats(C.Structure):
@@ -69,7 +70,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 # Every symbol the headers declare; tests check the library exports each one.
 EXPORTS = ["aci_create", "aci_destroy", "aci_last_error", "aci_opts_default", "aci_elementwise",
-           "aci_elementwise_ex", "aci_tt_release", "aci_k_frame_gemm", "aci_k_pi_block",
+           "aci_elementwise_ex", "aci_elementwise_batch", "aci_tt_release", "aci_k_frame_gemm", "aci_k_pi_block",
            "aci_k_frame_gemm_prec", "aci_k_pi_block_prec", "aci_k_prrlu", "aci_k_prrlu_rook",
            "aci_k_tt_random", "aci_k_apply_pinv", "aci_k_prrlu_static", "aci_k_reciprocal"]
 
@@ -102,6 +103,9 @@ def load_library(build_if_missing: bool = True) -> C.CDLL:
     lib.aci_elementwise_ex.argtypes = [vp, C.POINTER(AciTT), C.POINTER(AciTT), AciOp, dbl, i32,
                                        C.POINTER(AciOpts), C.POINTER(AciTT), C.POINTER(AciStats)]
     lib.aci_tt_release.argtypes = [vp, C.POINTER(AciTT)]
+    lib.aci_elementwise_batch.argtypes = [vp, i32, C.POINTER(AciTT), C.POINTER(AciTT), C.POINTER(AciOp),
+                                          C.POINTER(dbl), C.POINTER(i32), C.POINTER(AciOpts), C.POINTER(AciTT),
+                                          C.POINTER(AciStats), C.POINTER(i32)]
     lib.aci_k_frame_gemm.argtypes = [vp, i32, vp, vp, i32, i32, i32, vp, vp, i32, i32, vp]
     lib.aci_k_frame_gemm_prec.argtypes = [vp, i32, i32, vp, vp, i32, i32, i32, vp, vp, i32, i32, vp]
     lib.aci_k_pi_block.argtypes = [vp, i32, i32, C.POINTER(vp), C.POINTER(vp), i32, i32,
@@ -269,6 +273,18 @@ class Context:
                                          make_op(op, coef), float(tol), int(max_rank), C.byref(opts),
                                          C.byref(out), C.byref(stats))
         self._check(st)
+        cores = self._take_output(out)
+        info = self._info(st, stats, ranks, eps, L)
+        if pivots:
+            info["pivot_rows"] = [[int(prow[b * max_rank + q]) for q in range(info["ranks"][b + 1])]
+                                  for b in range(L - 1)]
+            info["pivot_cols"] = [[int(pcol[b * max_rank + q]) for q in range(info["ranks"][b + 1])]
+                                  for b in range(L - 1)]
+        return cores, info
+
+    def _take_output(self, out):
+        """Copy an output TT into numpy (host) or torch (device) cores and release it."""
+        import torch
         cores = []
         is_c = out.dtype == ACI_C128
         for s in range(out.L):
@@ -286,7 +302,11 @@ class Context:
                 t = t.view(torch.complex128 if is_c else torch.float64).view(shape)
                 cores.append(t)
         self.lib.aci_tt_release(self.handle, C.byref(out))
-        info = dict(status=STATUS[st], iterations=stats.iterations, converged=bool(stats.converged),
+        return cores
+
+    @staticmethod
+    def _info(st, stats, ranks, eps, L):
+        return dict(status=STATUS[st], iterations=stats.iterations, converged=bool(stats.converged),
                     fixed_point=bool(stats.fixed_point), max_eps=stats.max_eps, scale=stats.scale,
                     tau=stats.tau, device_ms=stats.device_ms, kernel_launches=stats.kernel_launches,
                     ranks=[int(ranks[i]) for i in range(L + 1)],
@@ -294,12 +314,53 @@ class Context:
                     kernels={k: dict(ms=stats.kernel_ms[i], count=int(stats.kernel_count[i]),
                                      flops=stats.kernel_flops[i], tensor_flops=stats.tensor_flops[i])
                              for i, k in enumerate(KERNEL_CLASSES)})
-        if pivots:
-            info["pivot_rows"] = [[int(prow[b * max_rank + q]) for q in range(info["ranks"][b + 1])]
-                                  for b in range(L - 1)]
-            info["pivot_cols"] = [[int(pcol[b * max_rank + q]) for q in range(info["ranks"][b + 1])]
-                                  for b in range(L - 1)]
-        return cores, info
+
+    def elementwise_batch(self, items, *, tol_kind="rel", max_sweeps=20, seed=0, out_memory="device",
+                          precision="fp64", pivot_mode="full", streams=0, profile=False):
+        """Independent products in one call. ``items``: list of dicts with keys a, b (None for
+        abs2_mul), op, tol, max_rank (and optional coef). Returns a list of (cores, info) with
+        info["status"] per product; raises only for call-level errors."""
+        n = len(items)
+        args = [(_TTArg(it["a"]), _TTArg(it["b"]) if it.get("b") is not None else None) for it in items]
+        A = (AciTT * max(n, 1))(*[x[0].tt for x in args])
+        has_b = any(x[1] is not None for x in args)
+        B = (AciTT * max(n, 1))(*[(x[1].tt if x[1] is not None else AciTT()) for x in args]) if has_b else None
+        ops = (AciOp * max(n, 1))(*[make_op(it.get("op", "mul"), it.get("coef")) for it in items])
+        tols = (C.c_double * max(n, 1))(*[float(it.get("tol", 1e-10)) for it in items])
+        mr = (C.c_int32 * max(n, 1))(*[int(it.get("max_rank", 64)) for it in items])
+        opts = AciOpts()
+        self.lib.aci_opts_default(C.byref(opts))
+        opts.tol_kind = TOL_KINDS[tol_kind]
+        opts.max_sweeps = int(max_sweeps)
+        opts.seed = int(seed)
+        opts.out_memory = ACI_MEM_HOST if out_memory == "host" else ACI_MEM_DEVICE
+        opts.profile = 1 if profile else 0
+        opts.precision = _precision_code(precision)
+        opts.pivot_mode = {"full": 0, "rook": 1}[pivot_mode]
+        opts.batch_streams = int(streams)
+        outs = (AciTT * max(n, 1))()
+        stats = (AciStats * max(n, 1))()
+        keep = []
+        for i, x in enumerate(args):
+            L = len(x[0].cores)
+            rk = (C.c_int64 * (L + 1))()
+            ep = (C.c_double * max(L - 1, 1))()
+            stats[i].ranks = C.cast(rk, C.POINTER(C.c_int64))
+            stats[i].eps = C.cast(ep, C.POINTER(C.c_double))
+            keep.append((rk, ep, L))
+        status = (C.c_int32 * max(n, 1))()
+        st = self.lib.aci_elementwise_batch(self.handle, n, A, B, ops, tols, mr, C.byref(opts), outs, stats, status)
+        results = []
+        for i in range(n):
+            rk, ep, L = keep[i]
+            if status[i] < 0:
+                results.append((None, dict(status=STATUS.get(status[i], status[i]))))
+                continue
+            cores = self._take_output(outs[i])
+            results.append((cores, self._info(status[i], stats[i], rk, ep, L)))
+        if st < 0 and all(status[i] >= 0 for i in range(n)):
+            self._check(st)
+        return results
 
     # ------------------------------------------------------------ step-level entry points
     def frame_gemm(self, A, B, arows=None, bcols=None, M=None, K=None, N=None, precision="fp64"):

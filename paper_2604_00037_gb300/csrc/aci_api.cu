@@ -19,6 +19,8 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <thread>
+#include <atomic>
 
 #include "../../include/aci.h"
 #include "../../include/aci_kernels.h"
@@ -45,6 +47,11 @@ struct aci_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> evfree;  // reusable events for per-kernel timing
     std::vector<cudaEvent_t> evall;
+    bool own_stream = false;          // a batch worker owns its stream
+    bool no_coop = false;             // a batch worker: no cooperative grids (others run beside it)
+    std::vector<aci_ctx*> workers;    // batch workers (own streams, scratch and graphs)
+    std::vector<cudaEvent_t> worker_ev;
+    cudaEvent_t evb = nullptr;
 };
 
 namespace {
@@ -146,6 +153,7 @@ struct Run {
     int L = 0, N = 0, chimax = 0, maxit = 20, rel = 1, prof = 0;
     int digits = 0;            // 0: FP64 contractions; 2..8: BF16 digit planes on the tensor cores
     int rook = 0;              // pivot search: 0 full, 1 rook
+    int no_coop = 0;           // concurrent batch worker: pivot searches stay within one cluster
     // per-kernel-class accounting (aci_kernel_class)
     double kms[4] = {0, 0, 0, 0};
     long long kcount[4] = {0, 0, 0, 0};
@@ -447,6 +455,7 @@ struct Run {
             a.Uld = ncap[b_store];
         }
         a.rook = rook;
+        a.no_coop = no_coop;
         a.tol = tol;
         a.rel = rel;
         a.smax = S;
@@ -902,6 +911,7 @@ aci_status run_typed(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, 
     R.prof = o.profile ? 1 : 0;
     R.digits = o.precision;
     R.rook = o.pivot_mode == ACI_PIVOT_ROOK ? 1 : 0;
+    R.no_coop = ctx->no_coop ? 1 : 0;
     R.seed = o.seed;
     R.op = make_op<T>(op);
     R.init = o.init;
@@ -946,6 +956,9 @@ aci_status aci_create(aci_ctx** ctx_out, int device, void* cuda_stream, aci_allo
 void aci_destroy(aci_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    for (aci_ctx* w : ctx->workers) aci_destroy(w);
+    for (cudaEvent_t e : ctx->worker_ev) cudaEventDestroy(e);
+    if (ctx->evb) cudaEventDestroy(ctx->evb);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->ws) dev_free(ctx, ctx->ws);
     if (!ctx->alloc) cudaStreamSynchronize(ctx->stream);
@@ -953,6 +966,7 @@ void aci_destroy(aci_ctx* ctx) {
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->evall) cudaEventDestroy(e);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
 
@@ -1023,6 +1037,85 @@ aci_status aci_elementwise_ex(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, ac
 aci_status aci_elementwise(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, double tol, int32_t max_rank,
                            aci_tt* out) {
     return aci_elementwise_ex(ctx, a, b, op, tol, max_rank, nullptr, out, nullptr);
+}
+
+aci_status aci_elementwise_batch(aci_ctx* ctx, int32_t n, const aci_tt* a, const aci_tt* b, const aci_op* op,
+                                 const double* tol, const int32_t* max_rank, const aci_opts* opts, aci_tt* out,
+                                 aci_stats* stats, aci_status* status) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    try {
+        if (n < 0 || (n > 0 && (!a || !op || !tol || !max_rank || !out))) fail(ctx, ACI_E_ARG, "bad arguments");
+        if (n == 0) return ACI_OK;
+        aci_opts o;
+        aci_opts_default(&o);
+        if (opts) o = *opts;
+        if (o.init) fail(ctx, ACI_E_ARG, "a batch takes no initial guess");
+        if (o.batch_streams < 0) fail(ctx, ACI_E_ARG, "batch_streams must be >= 0");
+        if (o.pivot_mode == ACI_PIVOT_ROOK) fail(ctx, ACI_E_ARG, "the rook search is a cooperative grid: not in a batch");
+        for (int i = 0; i < n; ++i) std::memset(&out[i], 0, sizeof(aci_tt));
+        int W = o.batch_streams > 0 ? o.batch_streams : std::max(1, ctx->num_sms / 16);
+        W = std::min(std::min(W, (int)n), 64);
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        if (!ctx->evb) ck(ctx, cudaEventCreateWithFlags(&ctx->evb, cudaEventDisableTiming), "event");
+        while ((int)ctx->workers.size() < W) {
+            cudaStream_t sw = nullptr;
+            ck(ctx, cudaStreamCreateWithFlags(&sw, cudaStreamNonBlocking), "worker stream");
+            aci_ctx* w = nullptr;
+            const aci_status cs = aci_create(&w, ctx->device, sw, ctx->alloc, ctx->free_fn, ctx->user);
+            if (cs != ACI_OK) {
+                cudaStreamDestroy(sw);
+                fail(ctx, cs, "worker context creation failed");
+            }
+            w->own_stream = true;
+            w->no_coop = true;
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                aci_destroy(w);
+                fail(ctx, ACI_E_CUDA, "worker event creation failed");
+            }
+            ctx->workers.push_back(w);
+            ctx->worker_ev.push_back(e);
+        }
+        // the workers start after the context stream's earlier work
+        ck(ctx, cudaEventRecord(ctx->evb, ctx->stream), "event");
+        for (int w = 0; w < W; ++w) ck(ctx, cudaStreamWaitEvent(ctx->workers[w]->stream, ctx->evb, 0), "stream wait");
+        std::atomic<int> next{0};
+        std::vector<aci_status> st(n, ACI_OK);
+        std::vector<std::string> msg(n);
+        auto work = [&](int w) {
+            cudaSetDevice(ctx->device);
+            aci_ctx* wc = ctx->workers[w];
+            for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) {
+                st[i] = aci_elementwise_ex(wc, &a[i], b ? &b[i] : nullptr, op[i], tol[i], max_rank[i], &o, &out[i],
+                                           stats ? &stats[i] : nullptr);
+                if (st[i] < 0) msg[i] = wc->err;
+            }
+        };
+        std::vector<std::thread> threads;
+        threads.reserve(W);
+        for (int w = 1; w < W; ++w) threads.emplace_back(work, w);
+        work(0);
+        for (auto& t : threads) t.join();
+        // the context stream waits for every worker
+        for (int w = 0; w < W; ++w) {
+            ck(ctx, cudaEventRecord(ctx->worker_ev[w], ctx->workers[w]->stream), "event");
+            ck(ctx, cudaStreamWaitEvent(ctx->stream, ctx->worker_ev[w], 0), "stream wait");
+        }
+        aci_status worst = ACI_OK;
+        for (int i = 0; i < n; ++i) {
+            if (status) status[i] = st[i];
+            if (st[i] < 0 && worst >= 0) {
+                worst = st[i];
+                ctx->err = "product " + std::to_string(i) + ": " + msg[i];
+            } else if (st[i] > 0 && worst == ACI_OK) {
+                worst = st[i];
+            }
+        }
+        return worst;
+    } catch (Fail& f) {
+        return f.st;
+    }
 }
 
 aci_status aci_tt_release(aci_ctx* ctx, aci_tt* out) {

@@ -97,6 +97,7 @@ template <class T> struct PrrluArgs {
     int mmax, nmax;     // capacities of this launch
     int* err;           // device error flags (DevErr)
     int rook;           // 1: rook search (W holds prrlu_rook_scratch_elems, ll prrlu_rook_ll_words(G); L, U required)
+    int no_coop;        // 1: no cooperative grid launch (the single-cluster kernel at every size)
     // filled by launch_prrlu
     int epc, wcap_elems, wcap_cols;
 };

@@ -1299,10 +1299,8 @@ size_t cluster_bytes(int mmax, int C, int wcap_elems, int wcap_cols, bool smemw)
 
 // Largest cluster (16, else 8) the device can schedule for the cluster kernel.
 template <class T>
-int max_cluster() {
-    static int v = 0;
-    if (v) return v;
-    v = 8;
+int max_cluster_query() {
+    int v = 8;
     auto fn = prrlu_cluster_kernel<T, true>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit) == cudaSuccess) {
@@ -1321,6 +1319,11 @@ int max_cluster() {
         if (cudaOccupancyMaxActiveClusters(&n, (void*)fn, &cfg) == cudaSuccess && n >= 1) v = 16;
     }
     cudaGetLastError();
+    return v;
+}
+template <class T>
+int max_cluster() {
+    static const int v = max_cluster_query<T>();  // once, thread-safe (concurrent batch workers)
     return v;
 }
 
@@ -1368,7 +1371,7 @@ cudaError_t launch_prrlu(const PrrluArgs<T>& a_in, int G, cudaStream_t st) {
         return cudaLaunchKernelEx(&cfg, fn, a);
     }
     const long long work = (long long)a.mmax * a.nmax * (cp ? 4 : 1);
-    if (work <= kClusterWorkMax) {
+    if (work <= kClusterWorkMax || a.no_coop) {  // no_coop: a single cluster at every size
         const int cmax = max_cluster<T>();
         int C = (int)std::min<long long>(cmax, std::max(1LL, (work + 4095) / 4096));
         C = std::max(C, std::min(cmax, (a.nmax + 31) / 32));  // at most 32 columns per CTA if possible

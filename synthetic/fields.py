@@ -174,6 +174,30 @@ CONFIG_NAMES = {
 }
 
 
+def batch_config4_spec(seed: int = 1004, n: int = 64):
+    """The batched workload: n independent pairs of 2D interleaved Fourier fields as in config 2,
+    with lengths L = 2 * nbits, nbits uniform in [10, 20] (L uniform over the even values in
+    [20, 40]), ranks chi uniform in [16, 256], ops alternating a*b and a*conj(b) (the same for
+    real fields). Each field has min(200, chi) modes, enough for its TT-SVD to reach rank chi.
+    The configuration fixes neither tolerance nor rank cap: tol 1e-8 (relative) and max_rank chi.
+    Returns the per-pair parameters; ``batch_config4_pair`` builds one pair."""
+    rng = np.random.default_rng(seed)
+    spec = []
+    for i in range(n):
+        nbits = int(rng.integers(10, 21))
+        chi = int(rng.integers(16, 257))
+        spec.append(dict(index=i, nbits=nbits, chi=chi, nmodes=min(200, chi),
+                         op="mul" if i % 2 == 0 else "mul_conj", tol=1e-8, max_rank=chi,
+                         seed_a=seed * 1000 + 2 * i, seed_b=seed * 1000 + 2 * i + 1))
+    return spec
+
+
+def batch_config4_pair(spec: dict):
+    a, _ = fourier_config2(spec["seed_a"], spec["chi"], nbits=spec["nbits"], nmodes=spec["nmodes"])
+    b, _ = fourier_config2(spec["seed_b"], spec["chi"], nbits=spec["nbits"], nmodes=spec["nmodes"])
+    return a, b
+
+
 def config_inputs(cfg: int, chi: int | None = None):
     """Inputs and call parameters for a workload; seeds A = 1000 + cfg, B = 2000 + cfg."""
     if cfg == 1:

@@ -1,0 +1,99 @@
+"""GPU checks of aci_elementwise_batch: independent products run concurrently on worker streams
+must give exactly what aci_elementwise_ex gives for each product alone (same kernels, same
+deterministic reductions), whatever the number of streams; a failing product reports its own
+status without disturbing the others. The whole method itself is pinned against the oracle by
+test_gpu_aci.py; one product of the batch is compared with the oracle here as well."""
+
+import numpy as np
+import pytest
+
+import oracle
+from synthetic.tt import tt_full, tt_random_uniform
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_00037_gb300.binding import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def dev(tt):
+    return [torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in tt]
+
+
+def make_items(seed, n):
+    """Uneven products: lengths 3-9, local dimensions 2-4, ranks 1-6, real and complex, several ops."""
+    rng = np.random.default_rng(seed)
+    items = []
+    for i in range(n):
+        L = int(rng.integers(3, 10))
+        d = int(rng.choice([2, 3, 4]))
+        cplx = bool(i % 3 == 2)
+        dt = np.complex128 if cplx else np.float64
+        a = tt_random_uniform(rng, L, d, int(rng.integers(1, 7)), dtype=dt, low=-1, high=1)
+        b = tt_random_uniform(rng, L, d, int(rng.integers(1, 7)), dtype=dt, low=-1, high=1)
+        op = ["mul", "mul_conj", "abs2_mul"][i % 3] if cplx else "mul"
+        items.append(dict(a=a, b=None if op == "abs2_mul" else b, op=op, tol=1e-12, max_rank=64))
+    return items
+
+
+def same(x, y):
+    return len(x) == len(y) and all(torch.equal(p, q) for p, q in zip(x, y))
+
+
+@pytest.mark.parametrize("streams", [1, 3, 0])
+def test_batch_equals_single_calls(ctx, streams):
+    items = make_items(1, 9)
+    res = ctx.elementwise_batch([dict(it, a=dev(it["a"]), b=dev(it["b"]) if it["b"] is not None else None)
+                                 for it in items], streams=streams)
+    for it, (cores, info) in zip(items, res):
+        assert info["status"] in ("ACI_OK", "ACI_W_NOT_CONVERGED")
+        ins = [dev(it["a"])] + ([dev(it["b"])] if it["b"] is not None else [None])
+        ref, rinfo = ctx.elementwise(*ins, op=it["op"], tol=it["tol"], max_rank=it["max_rank"])
+        assert same(cores, ref)
+        assert info["ranks"] == rinfo["ranks"] and info["iterations"] == rinfo["iterations"]
+
+
+def test_batch_product_matches_oracle_and_exact(ctx):
+    items = make_items(2, 4)
+    res = ctx.elementwise_batch([dict(it, a=dev(it["a"]), b=dev(it["b"]) if it["b"] is not None else None)
+                                 for it in items], streams=4)
+    it, (cores, info) = items[0], res[0]
+    ref = oracle.aci([it["a"], it["b"]], it["op"], it["tol"], it["max_rank"])
+    y = tt_full([c.cpu().numpy() for c in cores])
+    assert info["ranks"] == ref["ranks"]
+    assert np.abs(y - tt_full(ref["Y"])).max() <= 1e-12 * np.abs(tt_full(ref["Y"])).max()
+    for it, (cores, info) in zip(items, res):
+        A = tt_full(it["a"])
+        B = tt_full(it["b"]) if it["b"] is not None else None
+        exact = {"mul": lambda: A * B, "mul_conj": lambda: A * np.conj(B), "abs2_mul": lambda: np.abs(A) ** 2 * A}[it["op"]]()
+        got = tt_full([c.cpu().numpy() for c in cores])
+        assert np.abs(got - exact).max() <= 1e-9 * np.abs(exact).max()
+
+
+def test_batch_reports_a_failing_product_alone(ctx):
+    items = make_items(3, 5)
+    bad = dict(items[2], max_rank=0)  # invalid: max_rank must be >= 1
+    batch = [dict(it, a=dev(it["a"]), b=dev(it["b"]) if it["b"] is not None else None) for it in items]
+    batch[2] = dict(bad, a=dev(bad["a"]), b=dev(bad["b"]) if bad["b"] is not None else None)
+    res = ctx.elementwise_batch(batch, streams=2)
+    assert res[2][1]["status"] == "ACI_E_ARG" and res[2][0] is None
+    for i in (0, 1, 3, 4):
+        assert res[i][1]["status"] in ("ACI_OK", "ACI_W_NOT_CONVERGED") and res[i][0] is not None
+
+
+def test_batch_empty_and_host_outputs(ctx):
+    assert ctx.elementwise_batch([]) == []
+    items = make_items(4, 3)
+    res = ctx.elementwise_batch([dict(it, a=dev(it["a"]), b=dev(it["b"]) if it["b"] is not None else None)
+                                 for it in items], out_memory="host", streams=2)
+    for it, (cores, info) in zip(items, res):
+        assert isinstance(cores[0], np.ndarray)
