@@ -110,8 +110,10 @@ typedef struct {
     int32_t out_memory;    /* aci_memory of the output cores (default device)              */
     int32_t profile;       /* 1: time every kernel with CUDA events on the context stream and
                               count its algorithmic flops (aci_stats.kernel_*); 0: off        */
-    int32_t batch_streams; /* aci_elementwise_batch: products in flight at once (0 = one per 16
-                              SMs, the width of the pivot search's thread-block cluster)       */
+    int32_t batch_streams; /* aci_elementwise_batch: products in flight at once; 0 = autotuned:
+                              per batch-size class (floor(log2 n)) the context tries 1, 2 and 3
+                              products per 16 SMs (the width of one pivot-search cluster) on
+                              successive calls, timing each, then keeps the fastest          */
     int32_t _pad2;
 } aci_opts;
 

@@ -19,6 +19,8 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <map>
+#include <chrono>
 #include <thread>
 #include <atomic>
 
@@ -52,6 +54,15 @@ struct aci_ctx {
     std::vector<aci_ctx*> workers;    // batch workers (own streams, scratch and graphs)
     std::vector<cudaEvent_t> worker_ev;
     cudaEvent_t evb = nullptr;
+    // Concurrency autotuner of aci_elementwise_batch (batch_streams = 0): per batch-size class
+    // (floor(log2 n)), the candidate stream counts are tried on successive calls, each timed on the
+    // host around the whole call; afterwards the best rate is used.
+    struct BatchTune {
+        std::vector<int> cand;
+        std::vector<double> rate;
+        int best = 0;
+    };
+    std::map<int, BatchTune> batch_tune;
 };
 
 namespace {
@@ -1054,7 +1065,16 @@ aci_status aci_elementwise_batch(aci_ctx* ctx, int32_t n, const aci_tt* a, const
         if (o.batch_streams < 0) fail(ctx, ACI_E_ARG, "batch_streams must be >= 0");
         if (o.pivot_mode == ACI_PIVOT_ROOK) fail(ctx, ACI_E_ARG, "the rook search is a cooperative grid: not in a batch");
         for (int i = 0; i < n; ++i) std::memset(&out[i], 0, sizeof(aci_tt));
-        int W = o.batch_streams > 0 ? o.batch_streams : std::max(1, ctx->num_sms / 16);
+        const int base = std::max(1, ctx->num_sms / 16);  // one pivot-search cluster per product
+        aci_ctx::BatchTune* tune = nullptr;
+        int W = o.batch_streams;
+        if (W == 0) {
+            int cls = 0;
+            while ((2 << cls) <= n) ++cls;
+            tune = &ctx->batch_tune[cls];
+            if (tune->cand.empty()) tune->cand = {base, 2 * base, 3 * base};
+            W = tune->rate.size() < tune->cand.size() ? tune->cand[tune->rate.size()] : tune->best;
+        }
         W = std::min(std::min(W, (int)n), 64);
         ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
         if (!ctx->evb) ck(ctx, cudaEventCreateWithFlags(&ctx->evb, cudaEventDisableTiming), "event");
@@ -1092,11 +1112,22 @@ aci_status aci_elementwise_batch(aci_ctx* ctx, int32_t n, const aci_tt* a, const
                 if (st[i] < 0) msg[i] = wc->err;
             }
         };
+        const auto t0 = std::chrono::steady_clock::now();
         std::vector<std::thread> threads;
         threads.reserve(W);
         for (int w = 1; w < W; ++w) threads.emplace_back(work, w);
         work(0);
         for (auto& t : threads) t.join();
+        if (tune && tune->rate.size() < tune->cand.size()) {  // a trial of the autotuner: record its rate
+            const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            tune->rate.push_back(n / std::max(sec, 1e-9));
+            if (tune->rate.size() == tune->cand.size()) {
+                size_t b = 0;
+                for (size_t i = 1; i < tune->rate.size(); ++i)
+                    if (tune->rate[i] > tune->rate[b]) b = i;
+                tune->best = tune->cand[b];
+            }
+        }
         // the context stream waits for every worker
         for (int w = 0; w < W; ++w) {
             ck(ctx, cudaEventRecord(ctx->worker_ev[w], ctx->workers[w]->stream), "event");

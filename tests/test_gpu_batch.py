@@ -97,3 +97,15 @@ def test_batch_empty_and_host_outputs(ctx):
                                  for it in items], out_memory="host", streams=2)
     for it, (cores, info) in zip(items, res):
         assert isinstance(cores[0], np.ndarray)
+
+
+def test_autotuned_concurrency_keeps_results(ctx):
+    """batch_streams = 0 tries several concurrency levels on successive calls (then keeps the
+    fastest); every call returns the same products."""
+    items = make_items(5, 6)
+    batch = [dict(it, a=dev(it["a"]), b=dev(it["b"]) if it["b"] is not None else None) for it in items]
+    first = ctx.elementwise_batch(batch, streams=0)
+    for _ in range(4):
+        again = ctx.elementwise_batch(batch, streams=0)
+        for (c1, i1), (c2, i2) in zip(first, again):
+            assert same(c1, c2) and i1["ranks"] == i2["ranks"]
