@@ -74,6 +74,27 @@ aci_status aci_k_prrlu_rook(aci_ctx *ctx, int32_t dtype, const void *Min, int32_
                             double tau, int32_t chimax, int32_t *piv_rows, int32_t *piv_cols,
                             void *D, void *L, void *U, int32_t *k_out, double *eps_out);
 
+/* The pivot-proposer network (not in the paper): a perceptron with two hidden layers of 128
+ * ReLU units and one logit, scoring candidate rows and columns of a Pi block. Parameters are one
+ * FP32 device vector for F inputs (1 <= F <= 16): W1 (128 x F), b1 (128), W2 (128 x 128), b2 (128),
+ * W3 (128), b3 (1), row-major; aci_k_mlp_param_count gives its length.
+ *  aci_k_mlp_forward  z[s] = W3 . relu(W2 relu(W1 X[s] + b1) + b2) + b3 for the n rows of X (n x F,
+ *                     row-major FP32, device); fp16_weights = 1 rounds every weight to FP16 first
+ *                     (the inference form), 0 uses FP32.
+ *  aci_k_mlp_grad     grad = d loss / d params (device, same layout) and *loss (host) of the mean
+ *                     weighted logistic loss over the n samples with labels y (0/1, device):
+ *                     weight pos_weight on y = 1, 1 otherwise. FP32 arithmetic, sums over samples
+ *                     by atomics (order-dependent rounding).
+ *  aci_k_mlp_adam     one Adam step (Kingma and Ba, 2015) at step t >= 1 on `count` parameters,
+ *                     updating params and the moment vectors m, v (device, zero before t = 1). */
+int64_t aci_k_mlp_param_count(int32_t F);
+aci_status aci_k_mlp_forward(aci_ctx *ctx, int32_t n, int32_t F, const float *X, const float *params,
+                             int32_t fp16_weights, float *z);
+aci_status aci_k_mlp_grad(aci_ctx *ctx, int32_t n, int32_t F, const float *X, const float *y,
+                          float pos_weight, const float *params, float *grad, double *loss);
+aci_status aci_k_mlp_adam(aci_ctx *ctx, int32_t count, float *params, const float *grad, float *m,
+                          float *v, int32_t t, float lr, float beta1, float beta2, float eps);
+
 /* Random initial guess Y^init (Algorithm 1 input; Sec. 2.6): fills cores[s]
  * (rank[s] x d[s] x rank[s+1]) with SplitMix64 uniforms in [-1, 1): real entry e of the
  * concatenated cores uses counter e, complex entry e uses 2e (re) and 2e+1 (im).

@@ -72,7 +72,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 EXPORTS = ["aci_create", "aci_destroy", "aci_last_error", "aci_opts_default", "aci_elementwise",
            "aci_elementwise_ex", "aci_elementwise_batch", "aci_tt_release", "aci_k_frame_gemm", "aci_k_pi_block",
            "aci_k_frame_gemm_prec", "aci_k_pi_block_prec", "aci_k_prrlu", "aci_k_prrlu_rook",
-           "aci_k_tt_random", "aci_k_apply_pinv", "aci_k_prrlu_static", "aci_k_reciprocal"]
+           "aci_k_tt_random", "aci_k_apply_pinv", "aci_k_prrlu_static", "aci_k_reciprocal",
+           "aci_k_mlp_param_count", "aci_k_mlp_forward", "aci_k_mlp_grad", "aci_k_mlp_adam"]
 
 _lib = None
 
@@ -120,9 +121,14 @@ def load_library(build_if_missing: bool = True) -> C.CDLL:
     lib.aci_k_reciprocal.argtypes = [vp, vp, i32, vp]
     lib.aci_k_prrlu_static.argtypes = [vp, i32, vp, i32, i32, dbl, i32, vp, vp, vp, vp, vp,
                                        C.POINTER(i32), C.POINTER(dbl)]
+    lib.aci_k_mlp_param_count.argtypes = [i32]
+    lib.aci_k_mlp_forward.argtypes = [vp, i32, i32, vp, vp, i32, vp]
+    lib.aci_k_mlp_grad.argtypes = [vp, i32, i32, vp, vp, C.c_float, vp, vp, C.POINTER(dbl)]
+    lib.aci_k_mlp_adam.argtypes = [vp, i32, vp, vp, vp, vp, i32, C.c_float, C.c_float, C.c_float, C.c_float]
     for name in EXPORTS:
-        if name not in ("aci_destroy", "aci_last_error", "aci_opts_default"):
+        if name not in ("aci_destroy", "aci_last_error", "aci_opts_default", "aci_k_mlp_param_count"):
             getattr(lib, name).restype = C.c_int
+    lib.aci_k_mlp_param_count.restype = C.c_int64
     _lib = lib
     return lib
 
@@ -415,6 +421,35 @@ class Context:
             out["L"] = Lm[:kk].T.cpu().numpy()  # column-major m x kcap stored as kcap rows of length m
             out["U"] = Um[:kk].cpu().numpy()
         return out
+
+    # ------------------------------------------------------------ pivot-proposer network
+    def mlp_param_count(self, F):
+        return int(self.lib.aci_k_mlp_param_count(int(F)))
+
+    def mlp_forward(self, X, params, fp16=False):
+        """Logits of the n rows of X (torch float32, n x F, device)."""
+        import torch
+        n, F = X.shape
+        z = torch.empty(n, dtype=torch.float32, device=X.device)
+        self._check(self.lib.aci_k_mlp_forward(self.handle, n, F, X.contiguous().data_ptr(), params.data_ptr(),
+                                               1 if fp16 else 0, z.data_ptr()))
+        return z
+
+    def mlp_grad(self, X, y, params, pos_weight=1.0):
+        """(loss, gradient) of the mean weighted logistic loss; y float32 0/1 on the device."""
+        import torch
+        n, F = X.shape
+        g = torch.empty_like(params)
+        loss = C.c_double()
+        self._check(self.lib.aci_k_mlp_grad(self.handle, n, F, X.contiguous().data_ptr(), y.contiguous().data_ptr(),
+                                            float(pos_weight), params.data_ptr(), g.data_ptr(), C.byref(loss)))
+        return loss.value, g
+
+    def mlp_adam(self, params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        """One Adam step in place on params, m, v (device float32)."""
+        self._check(self.lib.aci_k_mlp_adam(self.handle, params.numel(), params.data_ptr(), grad.data_ptr(),
+                                            m.data_ptr(), v.data_ptr(), int(t), float(lr), float(beta1),
+                                            float(beta2), float(eps)))
 
     def tt_random(self, seed, ranks, dims, complex_values=False):
         import torch

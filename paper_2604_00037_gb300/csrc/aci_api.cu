@@ -1452,6 +1452,64 @@ aci_status aci_k_prrlu_rook(aci_ctx* ctx, int32_t dtype, const void* Min, int32_
     return k_prrlu(ctx, 1, dtype, Min, m, n, tau, chimax, piv_rows, piv_cols, D, L, U, k_out, eps_out);
 }
 
+int64_t aci_k_mlp_param_count(int32_t F) {
+    return (F >= 1 && F <= aci::kMlpMaxInputs) ? (int64_t)aci::mlp_param_count(F) : -1;
+}
+
+aci_status aci_k_mlp_forward(aci_ctx* ctx, int32_t n, int32_t F, const float* X, const float* params,
+                             int32_t fp16_weights, float* z) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    try {
+        if (n < 0 || F < 1 || F > aci::kMlpMaxInputs || (n > 0 && (!X || !params || !z)))
+            fail(ctx, ACI_E_ARG, "bad arguments");
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        aci::launch_mlp_forward(n, F, X, params, fp16_weights ? 1 : 0, z, nullptr, nullptr, ctx->stream);
+        note_launch(ctx, "mlp_forward");
+        ck(ctx, cudaStreamSynchronize(ctx->stream), "mlp_forward");
+        return ACI_OK;
+    } catch (Fail& f) {
+        return f.st;
+    }
+}
+
+aci_status aci_k_mlp_grad(aci_ctx* ctx, int32_t n, int32_t F, const float* X, const float* y, float pos_weight,
+                          const float* params, float* grad, double* loss) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    try {
+        if (n < 1 || F < 1 || F > aci::kMlpMaxInputs || !X || !y || !params || !grad || !loss || !(pos_weight > 0))
+            fail(ctx, ACI_E_ARG, "bad arguments");
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        char* ws = workspace(ctx, 256 + sizeof(float) * aci::mlp_train_scratch(n));
+        double* dloss = reinterpret_cast<double*>(ws);
+        float* scratch = reinterpret_cast<float*>(ws + 256);
+        aci::launch_mlp_grad(n, F, X, y, pos_weight, params, grad, dloss, scratch, ctx->stream);
+        note_launch(ctx, "mlp_grad");
+        ck(ctx, cudaMemcpyAsync(loss, dloss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "loss");
+        ck(ctx, cudaStreamSynchronize(ctx->stream), "mlp_grad");
+        return ACI_OK;
+    } catch (Fail& f) {
+        return f.st;
+    }
+}
+
+aci_status aci_k_mlp_adam(aci_ctx* ctx, int32_t count, float* params, const float* grad, float* m, float* v,
+                          int32_t t, float lr, float beta1, float beta2, float eps) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    try {
+        if (count < 0 || t < 1 || (count > 0 && (!params || !grad || !m || !v))) fail(ctx, ACI_E_ARG, "bad arguments");
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        aci::launch_mlp_adam(count, params, grad, m, v, t, lr, beta1, beta2, eps, ctx->stream);
+        note_launch(ctx, "mlp_adam");
+        ck(ctx, cudaStreamSynchronize(ctx->stream), "mlp_adam");
+        return ACI_OK;
+    } catch (Fail& f) {
+        return f.st;
+    }
+}
+
 aci_status aci_k_tt_random(aci_ctx* ctx, int32_t dtype, uint64_t seed, int32_t L, const int32_t* d,
                            const int64_t* rank, void* const* cores) {
     if (!ctx) return ACI_E_ARG;

@@ -117,6 +117,19 @@ size_t prrlu_ll_words(int mmax, int G, bool cplx_values);
 // y[i] = 1 / x[i] with the reciprocal the pivot search uses (step-level entry point).
 void launch_recip(const double* x, int n, double* y, cudaStream_t st);
 
+// The pivot-proposer network (aci_mlp.cu): F <= kMlpMaxInputs inputs, two hidden layers of
+// kMlpHidden units, one logit; parameters flat FP32 (W1, b1, W2, b2, W3, b3).
+constexpr int kMlpHidden = 128;
+constexpr int kMlpMaxInputs = 16;
+size_t mlp_param_count(int F);
+size_t mlp_train_scratch(int n);  // floats of scratch for launch_mlp_grad
+void launch_mlp_forward(int n, int F, const float* X, const float* P, int fp16, float* z, float* a1, float* a2,
+                        cudaStream_t st);
+void launch_mlp_grad(int n, int F, const float* X, const float* y, float pos_weight, const float* P, float* G,
+                     double* loss, float* scratch, cudaStream_t st);
+void launch_mlp_adam(int count, float* p, const float* g, float* m, float* v, int t, float lr, float b1, float b2,
+                     float eps, cudaStream_t st);
+
 // Per-bond buffers used by the output assembly.
 template <class T> struct BondBuf {
     const T* Pi;   // m_b x n_b row-major
