@@ -64,7 +64,14 @@ typedef enum { ACI_TOL_REL = 0, ACI_TOL_ABS = 1 } aci_tol_kind;
  *                  until a fixed point or the fourth hop. O((m + n) p) work per step instead of
  *                  O(m n); the error estimate is the rejected rook pivot's magnitude. Requires
  *                  min(m, n, max_rank) <= 4096 (real) / 2048 (complex) per bond. */
-typedef enum { ACI_PIVOT_FULL = 0, ACI_PIVOT_ROOK = 1 } aci_pivot_mode;
+/*  ACI_PIVOT_PROPOSED  (not in the paper) the learned proposer of aci_set_proposer restricts the
+ *                  left-to-right sweeps: per bond it scores the candidate rows and columns of the
+ *                  Pi block from cheap features (environment norms, local index, parent pivot
+ *                  position, bond, previous membership), keeps the ceil(keep * k_prev) + 8 best
+ *                  of each, forms Pi on them only and runs the full search there. Right-to-left
+ *                  sweeps stay the full search: they produce the output and the error estimates
+ *                  of the stop test, so plain ACI remains the judge and the fallback. */
+typedef enum { ACI_PIVOT_FULL = 0, ACI_PIVOT_ROOK = 1, ACI_PIVOT_PROPOSED = 2 } aci_pivot_mode;
 /* Arithmetic of the contractions (the frame half-products of Algorithm 5 and the Pi blocks of
  * Eq. (pifromframes)). The pivot search (Algorithm 2), its Schur updates and error estimates and
  * the output assembly Y = T P^-1 run in FP64 / complex128 in every mode.
@@ -211,6 +218,18 @@ aci_status aci_elementwise_batch(aci_ctx *ctx, int32_t n, const aci_tt *a, const
                                  const aci_op *op, const double *tol, const int32_t *max_rank,
                                  const aci_opts *opts, aci_tt *out, aci_stats *stats,
                                  aci_status *status);
+
+/* The learned proposer of ACI_PIVOT_PROPOSED: `params` is a device FP32 parameter vector of the
+ * network of aci_k_mlp_forward (include/aci_kernels.h) with nfeatures = 7, kept by the caller
+ * while the context uses it (NULL clears it); keep >= 1 sets the kept count ceil(keep * k_prev) + 8
+ * per side and bond. Inference rounds the weights to FP16. */
+aci_status aci_set_proposer(aci_ctx *ctx, const float *params, int32_t nfeatures, float keep);
+
+/* Training data for the proposer: while set, every full left-to-right local update appends one
+ * record per candidate row and column, the 7 features then 1 if it became a pivot else 0
+ * (8 floats), to the device buffer `buf` (capacity records); *count (device, zeroed by the
+ * caller) counts the records requested, of which the first `capacity` are stored. NULL stops. */
+aci_status aci_set_proposer_record(aci_ctx *ctx, float *buf, int64_t capacity, uint64_t *count);
 
 /* Free the library-owned parts of an output TT and zero the struct. */
 aci_status aci_tt_release(aci_ctx *ctx, aci_tt *out);

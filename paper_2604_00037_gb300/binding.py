@@ -53,6 +53,9 @@ class AciStats(C.Structure):
 
 KERNEL_CLASSES = ("frame", "pi", "pivot", "other")
 
+PIVOT_MODES = {"full": 0, "rook": 1, "proposed": 2}
+PROPOSER_FEATURES = 7
+
 # aci_precision: "fp64", or "bf16xS" for S = 2..8 exact BF16 digit planes on the tensor cores.
 PRECISIONS = {"fp64": 0, **{f"bf16x{s}": s for s in range(2, 9)}}
 
@@ -73,7 +76,8 @@ EXPORTS = ["aci_create", "aci_destroy", "aci_last_error", "aci_opts_default", "a
            "aci_elementwise_ex", "aci_elementwise_batch", "aci_tt_release", "aci_k_frame_gemm", "aci_k_pi_block",
            "aci_k_frame_gemm_prec", "aci_k_pi_block_prec", "aci_k_prrlu", "aci_k_prrlu_rook",
            "aci_k_tt_random", "aci_k_apply_pinv", "aci_k_prrlu_static", "aci_k_reciprocal",
-           "aci_k_mlp_param_count", "aci_k_mlp_forward", "aci_k_mlp_grad", "aci_k_mlp_adam"]
+           "aci_k_mlp_param_count", "aci_k_mlp_forward", "aci_k_mlp_grad", "aci_k_mlp_adam",
+           "aci_set_proposer", "aci_set_proposer_record"]
 
 _lib = None
 
@@ -122,6 +126,8 @@ def load_library(build_if_missing: bool = True) -> C.CDLL:
     lib.aci_k_prrlu_static.argtypes = [vp, i32, vp, i32, i32, dbl, i32, vp, vp, vp, vp, vp,
                                        C.POINTER(i32), C.POINTER(dbl)]
     lib.aci_k_mlp_param_count.argtypes = [i32]
+    lib.aci_set_proposer.argtypes = [vp, vp, i32, C.c_float]
+    lib.aci_set_proposer_record.argtypes = [vp, vp, i64, vp]
     lib.aci_k_mlp_forward.argtypes = [vp, i32, i32, vp, vp, i32, vp]
     lib.aci_k_mlp_grad.argtypes = [vp, i32, i32, vp, vp, C.c_float, vp, vp, C.POINTER(dbl)]
     lib.aci_k_mlp_adam.argtypes = [vp, i32, vp, vp, vp, vp, i32, C.c_float, C.c_float, C.c_float, C.c_float]
@@ -257,7 +263,7 @@ class Context:
         opts.out_memory = ACI_MEM_HOST if out_memory == "host" else ACI_MEM_DEVICE
         opts.profile = 1 if profile else 0
         opts.precision = _precision_code(precision)
-        opts.pivot_mode = {"full": 0, "rook": 1}[pivot_mode]
+        opts.pivot_mode = PIVOT_MODES[pivot_mode]
         It = None
         if init is not None:
             It = _TTArg(init)
@@ -342,7 +348,7 @@ class Context:
         opts.out_memory = ACI_MEM_HOST if out_memory == "host" else ACI_MEM_DEVICE
         opts.profile = 1 if profile else 0
         opts.precision = _precision_code(precision)
-        opts.pivot_mode = {"full": 0, "rook": 1}[pivot_mode]
+        opts.pivot_mode = PIVOT_MODES[pivot_mode]
         opts.batch_streams = int(streams)
         outs = (AciTT * max(n, 1))()
         stats = (AciStats * max(n, 1))()
@@ -421,6 +427,28 @@ class Context:
             out["L"] = Lm[:kk].T.cpu().numpy()  # column-major m x kcap stored as kcap rows of length m
             out["U"] = Um[:kk].cpu().numpy()
         return out
+
+    # ------------------------------------------------------------ learned proposer
+    def set_proposer(self, params, keep=1.25):
+        """Use the network `params` (device float32, kept alive here) for pivot_mode="proposed"."""
+        self._proposer = params
+        self._check(self.lib.aci_set_proposer(self.handle, params.data_ptr() if params is not None else None,
+                                              PROPOSER_FEATURES, float(keep)))
+
+    def record_proposer_data(self, capacity):
+        """Start recording (features, label) pairs of full left-to-right updates; returns a reader."""
+        import torch
+        buf = torch.zeros((capacity, PROPOSER_FEATURES + 1), dtype=torch.float32, device=self.device)
+        cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self._record = (buf, cnt)
+        self._check(self.lib.aci_set_proposer_record(self.handle, buf.data_ptr(), capacity, cnt.data_ptr()))
+
+        def read(stop=True):
+            n = min(int(cnt.item()), capacity)
+            if stop:
+                self._check(self.lib.aci_set_proposer_record(self.handle, None, 0, None))
+            return buf[:n, :PROPOSER_FEATURES].clone(), buf[:n, PROPOSER_FEATURES].clone(), int(cnt.item())
+        return read
 
     # ------------------------------------------------------------ pivot-proposer network
     def mlp_param_count(self, F):

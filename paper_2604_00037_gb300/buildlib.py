@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libaci_gb300.so")
-SOURCES = ["aci_api.cu", "aci_gemm.cu", "aci_prrlu.cu", "aci_misc.cu", "aci_noalloc.cu", "aci_tc.cu", "aci_mlp.cu"]
+SOURCES = ["aci_api.cu", "aci_gemm.cu", "aci_prrlu.cu", "aci_misc.cu", "aci_noalloc.cu", "aci_tc.cu", "aci_mlp.cu", "aci_proposer.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills",
          "--expt-relaxed-constexpr"]

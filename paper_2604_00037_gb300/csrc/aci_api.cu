@@ -63,6 +63,12 @@ struct aci_ctx {
         int best = 0;
     };
     std::map<int, BatchTune> batch_tune;
+    // learned proposer (ACI_PIVOT_PROPOSED) and training-data recording
+    const float* prop_params = nullptr;
+    float prop_keep = 1.25f;
+    float* rec_buf = nullptr;
+    long long rec_cap = 0;
+    unsigned long long* rec_count = nullptr;
 };
 
 namespace {
@@ -165,6 +171,13 @@ struct Run {
     int digits = 0;            // 0: FP64 contractions; 2..8: BF16 digit planes on the tensor cores
     int rook = 0;              // pivot search: 0 full, 1 rook
     int no_coop = 0;           // concurrent batch worker: pivot searches stay within one cluster
+    int proposed = 0;          // ACI_PIVOT_PROPOSED: learned candidate restriction in left-to-right sweeps
+    bool recording = false;    // append (features, pivot-or-not) of full left-to-right sweeps
+    float* pfeat = nullptr;    // proposer features, (mcap + ncap) x kPropFeatures
+    float* pscore = nullptr;   // proposer scores
+    int* psel_rows = nullptr;
+    int* psel_cols = nullptr;
+    size_t pcand = 1;          // largest mcap + ncap
     // per-kernel-class accounting (aci_kernel_class)
     double kms[4] = {0, 0, 0, 0};
     long long kcount[4] = {0, 0, 0, 0};
@@ -306,7 +319,7 @@ struct Run {
         }
         Minit[0] = c.take<T>(minit);
         Minit[1] = c.take<T>(minit);
-        chi = c.take<int>(L + 1);
+        chi = c.take<int>(L + 3);  // ranks, then the proposer's kept row / column counts
         chi_prev = c.take<int>(L + 1);
         dd = c.take<int>(L);
         err = c.take<int>(1);
@@ -324,6 +337,12 @@ struct Run {
         gcount = c.take<int>(gcount_n);
         tcbuf = c.take<unsigned char>(tc_bytes);
         bonds_dev = c.take<aci::BondBuf<T>>(std::max(nb, 1));
+        if (proposed || recording) {
+            pfeat = c.take<float>(pcand * aci::kPropFeatures);
+            pscore = c.take<float>(pcand);
+            psel_rows = c.take<int>(pcand);
+            psel_cols = c.take<int>(pcand);
+        }
         Yptr_dev = c.take<T*>(L);
         pcol_dev = c.take<int*>(std::max(nb, 1));
         jprev_dev = c.take<int*>(std::max(nb, 1));
@@ -379,6 +398,7 @@ struct Run {
             wcap = std::max(wcap, (size_t)mcap[b] * ncap[b]);
             mmax_all = std::max(mmax_all, mcap[b]);
             size_pivot_search(mcap[b], ncap[b]);
+            pcand = std::max(pcand, (size_t)mcap[b] + ncap[b]);
             if ((long long)mcap[b] * ncap[b] >= (1LL << 31))
                 fail(ctx, ACI_E_SHAPE, "a Pi block would exceed 2^31 entries");
         }
@@ -502,6 +522,102 @@ struct Run {
         gemm(g, mcap[b], ncap[b], kmax_of(b + 1), "pi_block", ACI_KCLASS_PI);
     }
 
+    // Candidate features of bond b (the proposer's inputs), from the operands of its Pi block.
+    void features(int b) {
+        aci::ProposerArgs<T> a;
+        std::memset(&a, 0, sizeof(a));
+        for (int n = 0; n < N; ++n) {
+            a.A[n] = (b == 0) ? Xp(n, 0) : LX[n][b];
+            a.B[n] = (b + 1 == L - 1) ? Xp(n, L - 1) : XR[n][b + 1];
+            a.K[n] = dimc(r[n][b + 1]);
+            a.lda[n] = dimc(r[n][b + 1]);
+            a.ldb[n] = dimr(d[b + 1], b + 2);
+        }
+        a.M = dimr(d[b], b);
+        a.N = dimr(d[b + 1], b + 2);
+        a.chi = chi;
+        a.nprod = N;
+        a.d_row = d[b];
+        a.d_col = d[b + 1];
+        a.chi_row = dimr(1, b);
+        a.chi_col = dimr(1, b + 2);
+        a.prev_rows = prow[b];
+        a.prev_cols = pcol[b];
+        a.kprev = dimr(1, b + 1);
+        a.bond_frac = L > 2 ? (float)b / (float)(L - 2) : 0.f;
+        a.X = pfeat;
+        a.mcap = mcap[b];
+        a.ncap = ncap[b];
+        cudaEvent_t e = pre(ACI_KCLASS_OTHER);
+        aci::launch_features<T>(a, st);
+        post(ACI_KCLASS_OTHER, e, "proposer features");
+    }
+
+    // The learned restriction of bond b: scores, kept rows/columns, Pi on them, prrLU, pivots mapped back.
+    void proposed_update(int b) {
+        features(b);
+        cudaEvent_t e = pre(ACI_KCLASS_OTHER);
+        aci::launch_mlp_forward(mcap[b] + ncap[b], aci::kPropFeatures, pfeat, ctx->prop_params, 1, pscore, nullptr,
+                                nullptr, st);
+        aci::TopkArgs t;
+        t.z = pscore;
+        t.M = dimr(d[b], b);
+        t.N = dimr(d[b + 1], b + 2);
+        t.kprev = dimr(1, b + 1);
+        t.chi = chi;
+        t.mcap = mcap[b];
+        t.ncap = ncap[b];
+        t.keep = ctx->prop_keep;
+        t.sel_rows = psel_rows;
+        t.sel_cols = psel_cols;
+        t.slot_rows = L + 1;
+        t.slot_cols = L + 2;
+        ck(ctx, aci::launch_topk(t, st), "proposer top-k");
+        ctx->launches++;
+        kcount[ACI_KCLASS_OTHER]++;
+        post(ACI_KCLASS_OTHER, e, "proposer score");
+        // Pi on the kept rows and columns (the same contraction, gathered on load)
+        aci::GemmArgs<T> g = gemm_base();
+        g.combine = 1;
+        g.nprod = N;
+        for (int n = 0; n < N; ++n) {
+            g.A[n] = (b == 0) ? Xp(n, 0) : LX[n][b];
+            g.B[n] = (b + 1 == L - 1) ? Xp(n, L - 1) : XR[n][b + 1];
+            g.K[n] = dimc(r[n][b + 1]);
+            g.lda[n] = dimc(r[n][b + 1]);
+            g.ldb[n] = dimr(d[b + 1], b + 2);
+        }
+        g.arow = psel_rows;
+        g.bcol = psel_cols;
+        g.M[0] = dimr(1, L + 1);
+        g.N[0] = dimr(1, L + 2);
+        g.C[0] = Pi[b];
+        g.smax = smax;
+        gemm(g, mcap[b], ncap[b], kmax_of(b + 1), "pi_block (proposed)", ACI_KCLASS_PI);
+        prrlu(Pi[b], dimr(1, L + 1), dimr(1, L + 2), mcap[b], ncap[b], b + 1, b, false, eps_lr + b, smax);
+        cudaEvent_t e2 = pre(ACI_KCLASS_OTHER);
+        aci::launch_map_pivots(chi, b + 1, prow[b], pcol[b], psel_rows, psel_cols, st);
+        post(ACI_KCLASS_OTHER, e2, "proposer map");
+    }
+
+    void record(int b) {
+        aci::RecordArgs rr;
+        rr.X = pfeat;
+        rr.M = dimr(d[b], b);
+        rr.N = dimr(d[b + 1], b + 2);
+        rr.k = dimr(1, b + 1);
+        rr.chi = chi;
+        rr.mcap = mcap[b];
+        rr.prow = prow[b];
+        rr.pcol = pcol[b];
+        rr.buf = ctx->rec_buf;
+        rr.capacity = ctx->rec_cap;
+        rr.count = ctx->rec_count;
+        cudaEvent_t e = pre(ACI_KCLASS_OTHER);
+        aci::launch_record(rr, st);
+        post(ACI_KCLASS_OTHER, e, "proposer record");
+    }
+
     // LX[n][b] = rows prow[b-1] of LX[n][b-1], times X^n_b (Leftframe of Algorithm 5).
     void left_half(int b) {
         if (b == 0) return;
@@ -571,10 +687,10 @@ struct Run {
         const int nb = L - 1;
 
         // constants and per-call state
-        std::vector<int> chi_h(L + 1, 0);
+        std::vector<int> chi_h(L + 3, 0);
         chi_h[0] = 1;
         chi_h[L] = 1;
-        ck(ctx, cudaMemcpyAsync(chi, chi_h.data(), sizeof(int) * (L + 1), cudaMemcpyHostToDevice, st), "init chi");
+        ck(ctx, cudaMemcpyAsync(chi, chi_h.data(), sizeof(int) * (L + 3), cudaMemcpyHostToDevice, st), "init chi");
         ck(ctx, cudaMemcpyAsync(dd, d.data(), sizeof(int) * L, cudaMemcpyHostToDevice, st), "init d");
         ck(ctx, cudaMemsetAsync(err, 0, sizeof(int), st), "memset");
         ck(ctx, cudaMemsetAsync(smax, 0, sizeof(unsigned long long), st), "memset");
@@ -690,9 +806,15 @@ struct Run {
             prrlu_launches = 0;
             for (int b = 0; b < nb; ++b) {  // left to right, CI "right"
                 left_half(b);
+                if (proposed) {  // the learned restriction; the full right-to-left sweep stays the judge
+                    proposed_update(b);
+                    continue;
+                }
+                if (recording) features(b);
                 pi_block(b);
                 prrlu(Pi[b], dimr(d[b], b), dimr(d[b + 1], b + 2), mcap[b], ncap[b], b + 1, b, false,
                       eps_lr + b, smax);
+                if (recording) record(b);
             }
             for (int b = nb - 1; b >= 0; --b) {  // right to left, CI "left"
                 right_half(b + 1);
@@ -923,6 +1045,9 @@ aci_status run_typed(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, 
     R.digits = o.precision;
     R.rook = o.pivot_mode == ACI_PIVOT_ROOK ? 1 : 0;
     R.no_coop = ctx->no_coop ? 1 : 0;
+    R.proposed = o.pivot_mode == ACI_PIVOT_PROPOSED ? 1 : 0;
+    R.recording = ctx->rec_buf != nullptr && !R.proposed;
+    if (R.proposed && !ctx->prop_params) fail(ctx, ACI_E_ARG, "ACI_PIVOT_PROPOSED needs aci_set_proposer");
     R.seed = o.seed;
     R.op = make_op<T>(op);
     R.init = o.init;
@@ -1009,7 +1134,8 @@ aci_status aci_elementwise_ex(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, ac
         if (opts) o = *opts;
         if (o.tol_kind != ACI_TOL_REL && o.tol_kind != ACI_TOL_ABS) fail(ctx, ACI_E_ARG, "bad tol_kind");
         if (o.max_sweeps < 1) fail(ctx, ACI_E_ARG, "max_sweeps must be >= 1");
-        if (o.pivot_mode != ACI_PIVOT_FULL && o.pivot_mode != ACI_PIVOT_ROOK) fail(ctx, ACI_E_ARG, "unsupported pivot mode");
+        if (o.pivot_mode != ACI_PIVOT_FULL && o.pivot_mode != ACI_PIVOT_ROOK && o.pivot_mode != ACI_PIVOT_PROPOSED)
+            fail(ctx, ACI_E_ARG, "unsupported pivot mode");
         if (!valid_precision(o.precision)) fail(ctx, ACI_E_ARG, "unsupported precision");
         if (o.out_memory != ACI_MEM_DEVICE && o.out_memory != ACI_MEM_HOST) fail(ctx, ACI_E_ARG, "bad out_memory");
         validate_tt(ctx, a, "a");
@@ -1450,6 +1576,35 @@ aci_status aci_k_prrlu_rook(aci_ctx* ctx, int32_t dtype, const void* Min, int32_
                             int32_t chimax, int32_t* piv_rows, int32_t* piv_cols, void* D, void* L, void* U,
                             int32_t* k_out, double* eps_out) {
     return k_prrlu(ctx, 1, dtype, Min, m, n, tau, chimax, piv_rows, piv_cols, D, L, U, k_out, eps_out);
+}
+
+aci_status aci_set_proposer(aci_ctx* ctx, const float* params, int32_t nfeatures, float keep) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    if (params && nfeatures != aci::kPropFeatures) {
+        ctx->err = "the proposer takes " + std::to_string(aci::kPropFeatures) + " features";
+        return ACI_E_ARG;
+    }
+    if (params && !(keep >= 1.0f)) {
+        ctx->err = "keep must be >= 1";
+        return ACI_E_ARG;
+    }
+    ctx->prop_params = params;
+    ctx->prop_keep = keep;
+    return ACI_OK;
+}
+
+aci_status aci_set_proposer_record(aci_ctx* ctx, float* buf, int64_t capacity, uint64_t* count) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    if (buf && (capacity < 1 || !count)) {
+        ctx->err = "bad arguments";
+        return ACI_E_ARG;
+    }
+    ctx->rec_buf = buf;
+    ctx->rec_cap = buf ? capacity : 0;
+    ctx->rec_count = buf ? reinterpret_cast<unsigned long long*>(count) : nullptr;
+    return ACI_OK;
 }
 
 int64_t aci_k_mlp_param_count(int32_t F) {

@@ -130,6 +130,51 @@ void launch_mlp_grad(int n, int F, const float* X, const float* y, float pos_wei
 void launch_mlp_adam(int count, float* p, const float* g, float* m, float* v, int t, float lr, float b1, float b2,
                      float eps, cudaStream_t st);
 
+// The learned proposer's device side (aci_proposer.cu).
+constexpr int kPropFeatures = 7;
+template <class T> struct ProposerArgs {
+    const T* A[2];        // Pi-A operands (rows = Pi rows), as the Pi block reads them
+    const T* B[2];        // Pi-B operands (columns = Pi columns)
+    DimE M, N, K[2], lda[2], ldb[2];
+    const int* chi;
+    int nprod;
+    int d_row, d_col;     // local dimensions of the bond's two sites
+    DimE chi_row, chi_col;  // chi_b (row parents), chi_{b+2} (column children)
+    const int* prev_rows;   // the bond's pivots of the previous sweep, kprev of them
+    const int* prev_cols;
+    DimE kprev;
+    float bond_frac;
+    float* X;             // (mcap + ncap) x kPropFeatures
+    int mcap, ncap;
+};
+template <class T> void launch_features(const ProposerArgs<T>& a, cudaStream_t st);
+struct TopkArgs {
+    const float* z;       // (mcap + ncap) scores
+    DimE M, N, kprev;
+    const int* chi;
+    int mcap, ncap;
+    float keep;
+    int* sel_rows;        // [mcap] kept row indices, ascending
+    int* sel_cols;        // [ncap]
+    int slot_rows, slot_cols;  // chi[slot] <- the kept counts
+};
+size_t topk_smem(int mcap, int ncap);
+cudaError_t launch_topk(const TopkArgs& t, cudaStream_t st);
+void launch_map_pivots(const int* chi, int kslot, int* prow, int* pcol, const int* sel_rows, const int* sel_cols,
+                       cudaStream_t st);
+struct RecordArgs {
+    const float* X;
+    DimE M, N, k;
+    const int* chi;
+    int mcap;
+    const int* prow;
+    const int* pcol;
+    float* buf;                 // records of kPropFeatures + 1 floats
+    long long capacity;         // records
+    unsigned long long* count;  // device counter (records requested so far)
+};
+void launch_record(const RecordArgs& r, cudaStream_t st);
+
 // Per-bond buffers used by the output assembly.
 template <class T> struct BondBuf {
     const T* Pi;   // m_b x n_b row-major
