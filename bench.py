@@ -59,7 +59,111 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="time this many independent pairs of the batched workload instead (aci_elementwise_batch)")
     ap.add_argument("--streams", type=int, default=0, help="batch: products in flight (0 = library default)")
+    ap.add_argument("--proposer", action="store_true",
+                    help="the learned-proposal sequence: train on steps 0-39, compare on 40-59")
+    ap.add_argument("--seq-steps", type=int, default=60)
+    ap.add_argument("--keep", type=float, default=1.25)
     return ap.parse_args()
+
+
+def _seq_pair(args):
+    t, chi = args
+    from synthetic.fields import sequence_config5_pair
+    return sequence_config5_pair(t, chi)
+
+
+def run_proposer(args):
+    """The learned-proposal sequence (synthetic/fields.py, sequence_config5_pair): products f_t g_t,
+    tol 1e-8, max_rank 2 chi. Plain ACI runs steps 0 .. 2/3 of the sequence while recording the
+    (features, pivot-or-not) pairs of its left-to-right updates; the network is trained on them with
+    the library's kernels (Adam, weighted logistic loss); the remaining steps run with plain ACI and
+    with the learned restriction. Reports time per product, the error of both against the exact
+    product on 20000 sampled points, and the recall of plain ACI's pivots by the kept candidates."""
+    import multiprocessing as mp
+    import numpy as np
+    nsteps = args.seq_steps
+    ntrain = (2 * nsteps) // 3
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:  # before any GPU call
+        pairs = pool.map(_seq_pair, [(t, args.chi) for t in range(nsteps)])
+    gen_s = time.time() - t0
+    print(f"proposer: {nsteps} steps generated in {gen_s:.1f} s", file=sys.stderr, flush=True)
+    import torch
+    from oracle import mlp
+    from paper_2604_00037_gb300.binding import Context
+    from synthetic.tt import tt_eval
+    ctx = Context(0)
+    tol, max_rank = 1e-8, 2 * args.chi
+    dev = lambda tt: [torch.from_numpy(c).cuda() for c in tt]
+    read = ctx.record_proposer_data(4_000_000)
+    for t in range(ntrain):
+        a, b = pairs[t]
+        ctx.elementwise(dev(a), dev(b), "mul", tol, max_rank, max_sweeps=args.max_sweeps)
+    X, y, nrec = read()
+    pos = float(y.mean().item())
+    P = torch.from_numpy(mlp.init(0, 7)).cuda()
+    M, V = torch.zeros_like(P), torch.zeros_like(P)
+    t1 = time.time()
+    for it in range(1, 401):
+        loss, g = ctx.mlp_grad(X, y, P, (1 - pos) / max(pos, 1e-6))
+        ctx.mlp_adam(P, g, M, V, it, 2e-3)
+    torch.cuda.synchronize()
+    train_s = time.time() - t1
+    print(f"proposer: {X.shape[0]} records ({pos:.3f} positive), loss {loss:.4f}, {train_s:.1f} s", file=sys.stderr,
+          flush=True)
+    rng = np.random.default_rng(8)
+    rows = {"plain": [], "proposed": []}
+    for t in range(ntrain, nsteps):
+        a, b = pairs[t]
+        pts = rng.integers(0, 2, size=(20000, len(a)))
+        exact = tt_eval(a, pts) * tt_eval(b, pts)
+        A, B = dev(a), dev(b)
+        for mode in ("plain", "proposed"):
+            if mode == "proposed":
+                ctx.set_proposer(P, keep=args.keep)
+            for rep in range(2):  # the second run is timed
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ycores, info = ctx.elementwise(A, B, "mul", tol, max_rank, max_sweeps=args.max_sweeps,
+                                               pivot_mode="proposed" if mode == "proposed" else "full")
+                e1.record()
+                torch.cuda.synchronize()
+            yv = tt_eval([c.cpu().numpy() for c in ycores], pts)
+            rows[mode].append((e0.elapsed_time(e1), float(np.abs(yv - exact).max() / np.abs(exact).max()),
+                               info["iterations"], max(info["ranks"])))
+            ctx.set_proposer(None)
+    summ = {m: {"ms_per_product": float(np.mean([r[0] for r in v])),
+                "max_rel_err_vs_exact": float(np.max([r[1] for r in v])),
+                "mean_iterations": float(np.mean([r[2] for r in v])),
+                "max_rank": int(np.max([r[3] for r in v]))} for m, v in rows.items()}
+    # recall: of plain ACI's pivots in recorded held-out data, the share the proposer keeps
+    read = ctx.record_proposer_data(2_000_000)
+    a, b = pairs[nsteps - 1]
+    ctx.elementwise(dev(a), dev(b), "mul", tol, max_rank, max_sweeps=args.max_sweeps)
+    Xt, yt, _ = read()
+    zt = ctx.mlp_forward(Xt, P, fp16=True).cpu().numpy()
+    yt = yt.cpu().numpy()
+    sub = np.random.default_rng(9)
+    zp, zn = zt[yt > 0.5], zt[yt < 0.5]
+    zp = zp[sub.permutation(len(zp))[:2000]]
+    zn = zn[sub.permutation(len(zn))[:2000]]
+    line = {"metric": "learned pivot proposal: ACI time per product at equal error (held-out steps)",
+            "unit": "ms/product", "value": summ["proposed"]["ms_per_product"], "higher_is_better": False,
+            "dtype": "f64", "data": "synthetic", "n_gpus": 1,
+            "config": {"workload": f"{nsteps}-step sequence f_t g_t of 2D interleaved Fourier fields (L=40, d=2, "
+                                   f"chi={args.chi}), phases advancing by omega_k t; tol {tol:g}, max_rank {max_rank}; "
+                                   f"trained on steps 0-{ntrain - 1}, compared on {ntrain}-{nsteps - 1}",
+                       "keep": args.keep, "input_generation_s": gen_s},
+            "training": {"records": int(X.shape[0]), "positive_share": pos, "final_loss": loss,
+                         "adam_steps": 400, "train_s": train_s},
+            "plain": summ["plain"], "proposed": summ["proposed"],
+            "speedup": summ["plain"]["ms_per_product"] / summ["proposed"]["ms_per_product"],
+            "held_out_auc": float((zp[:, None] > zn[None, :]).mean()) if len(zp) and len(zn) else float("nan")}
+    print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 def _make_pair(spec):
@@ -313,6 +417,8 @@ def main():
         return run_kernel(args)
     if args.batch:
         return run_batch(args)
+    if args.proposer:
+        return run_proposer(args)
     import numpy as np
     import torch
     import torch.distributed as dist

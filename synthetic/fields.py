@@ -174,6 +174,27 @@ CONFIG_NAMES = {
 }
 
 
+def sequence_config5_pair(t: int, chi: int, nbits: int = 20, nmodes: int = 200, kmax: int = 32, seed: int = 1005):
+    """Step t of the learned-proposal sequence: f_t and g_t are 2D interleaved Fourier fields as in
+    config 2 whose every mode's phase advances by omega_k t, omega_k ~ U[0, 1] (the modes, amplitudes,
+    initial phases and omegas fixed by ``seed``); TT-SVD to rank chi."""
+    out = []
+    for which in (0, 1):
+        rng = np.random.default_rng(seed * 10 + which)
+        L = 2 * nbits
+        lat = _disc_lattice(2, kmax)
+        idx = rng.choice(len(lat), size=nmodes, replace=False)
+        kv = lat[idx]
+        amp = rng.standard_normal(nmodes) * np.exp(-(kv.astype(float) ** 2).sum(axis=1) / 100.0)
+        phase0 = rng.uniform(0.0, 2 * np.pi, size=nmodes)
+        omega = rng.uniform(0.0, 1.0, size=nmodes)
+        phase = phase0 + omega * t
+        modes = [cos_mode_tt(amp[i], phase[i], _site_angles(kv[i], L, 2, "interleaved", 2 * np.pi))
+                 for i in range(nmodes)]
+        out.append(tt_svd_round(tt_block_sum(modes), max_rank=chi))
+    return out[0], out[1]
+
+
 def batch_config4_spec(seed: int = 1004, n: int = 64):
     """The batched workload: n independent pairs of 2D interleaved Fourier fields as in config 2,
     with lengths L = 2 * nbits, nbits uniform in [10, 20] (L uniform over the even values in
