@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--mixed-digits", type=int, default=6, help="BF16 digit planes of the mixed run (0: skip it)")
     ap.add_argument("--precision", default="fp64", help="contractions of the headline run: fp64 or bf16xS")
     ap.add_argument("--pivot-mode", default="full", choices=["full", "rook"])
+    ap.add_argument("--overlap", default="auto", choices=["auto", "off", "on"],
+                    help="schedule of the sweeps (aci_opts.sweep_overlap)")
     ap.add_argument("--kernel", default="", choices=["", "pi_block", "frame_gemm", "prrlu"],
                     help="time one step-level call of this shape instead of the product (kernel profiling)")
     ap.add_argument("--m", type=int, default=2048)
@@ -285,7 +287,7 @@ def config_dict(args, p):
                         f"a*b, tol {p['tol']:g} rel, max_rank {p['max_rank']}, <= {args.max_sweeps} sweeps",
             "L": 40, "d": 2, "chi": args.chi, "max_rank": p["max_rank"], "tol": p["tol"],
             "op": "a*b", "max_sweeps": args.max_sweeps,
-            "contractions": args.precision, "pivot_search": args.pivot_mode,
+            "contractions": args.precision, "pivot_search": args.pivot_mode, "sweep_overlap": args.overlap,
             "l2": "flushed before every timed step (256 MB write, untimed)",
             "parallelism": f"replicas x{args.gpus}"}
 
@@ -441,7 +443,7 @@ def main():
 
     def step(profile):
         return ctx.elementwise(A, B, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps, profile=profile,
-                               precision=args.precision, pivot_mode=args.pivot_mode)
+                               precision=args.precision, pivot_mode=args.pivot_mode, overlap=args.overlap)
 
     for w in range(args.warmup):
         flush.fill_(w & 0xFF)
@@ -499,14 +501,16 @@ def main():
     ah = [torch.from_numpy(c).pin_memory().numpy() for c in a]
     bh = [torch.from_numpy(c).pin_memory().numpy() for c in b]
     h2d = sum(c.nbytes for c in ah) + sum(c.nbytes for c in bh)
-    ctx.elementwise(ah, bh, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps, out_memory="host")
+    ctx.elementwise(ah, bh, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps, out_memory="host",
+                    precision=args.precision, pivot_mode=args.pivot_mode, overlap=args.overlap)
     e2e_t, d2h = [], 0
     for k in range(max(1, min(args.steps, 3))):
         flush.fill_(k & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         yh, _ = ctx.elementwise(ah, bh, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps,
-                                out_memory="host")
+                                out_memory="host", precision=args.precision, pivot_mode=args.pivot_mode,
+                                overlap=args.overlap)
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
         d2h = sum(c.nbytes for c in yh)
@@ -528,7 +532,7 @@ def main():
 
         def mstep(profile):
             return ctx.elementwise(A, B, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps, profile=profile,
-                                   precision=prec)
+                                   precision=prec, overlap=args.overlap)
         mstep(False)
         mt, minfo = [], []
         for k in range(args.steps):

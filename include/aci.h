@@ -121,8 +121,23 @@ typedef struct {
                               per batch-size class (floor(log2 n)) the context tries 1, 2 and 3
                               products per 16 SMs (the width of one pivot-search cluster) on
                               successive calls, timing each, then keeps the fastest          */
-    int32_t _pad2;
+    int32_t sweep_overlap; /* aci_overlap: schedule of the sweeps (results agree to rounding)    */
 } aci_opts;
+
+/* Schedule of the sweeps (aci_opts.sweep_overlap). The frame half-products and the Pi block of a
+ * bond depend on the previous bond's pivots only through a row (left-to-right) or column (right-
+ * to-left) selection. The overlapped schedule computes them for every candidate row or column on
+ * a second stream while the previous bond's pivot search runs, then gathers the selected ones:
+ * d_b times the contraction work, taken off the critical path of the sweep. Results differ from
+ * the plain schedule only by the rounding of the contractions (their K splits differ).
+ *  ACI_OVERLAP_AUTO  overlapped when every local dimension is 2 and the call is neither a
+ *                    learned-proposal call (ACI_PIVOT_PROPOSED) nor recording proposer data,
+ *                    nor one product of aci_elementwise_batch (whose products already fill the
+ *                    GPU); plain otherwise
+ *  ACI_OVERLAP_OFF   plain: every step on the context stream, in order
+ *  ACI_OVERLAP_ON    overlapped wherever it applies (L >= 3; not with ACI_PIVOT_PROPOSED or
+ *                    recording, which keep the plain left-to-right sweep)                    */
+typedef enum { ACI_OVERLAP_AUTO = 0, ACI_OVERLAP_OFF = 1, ACI_OVERLAP_ON = 2 } aci_overlap;
 
 /* Kernel classes of aci_stats.kernel_* (profile = 1). Flops are real-equivalent (a complex
  * multiply-add counts 8) and algorithmic: what the step needs, not what the kernel issues. */
@@ -203,7 +218,8 @@ aci_status aci_elementwise_ex(aci_ctx *ctx, const aci_tt *a, const aci_tt *b, ac
 /* Independent products in one call (no counterpart in the paper: a throughput form of
  * aci_elementwise_ex for many pairs of uneven length and rank). Product i is
  * f(a[i], b[i]) with op[i], tol[i], max_rank[i] and the shared opts (opts->init must be NULL),
- * exactly as aci_elementwise_ex would compute it: same kernels, same results bit for bit.
+ * exactly as aci_elementwise_ex would compute it with the schedule the batch uses: same kernels,
+ * same results bit for bit. In a batch ACI_OVERLAP_AUTO is the plain schedule (ACI_OVERLAP_OFF).
  * Up to opts->batch_streams products run at once, each on a worker stream of the context with its
  * own scratch and CUDA graphs, driven by a host thread; workers take the next product as they
  * finish, so uneven products balance. The pivot search of one product keeps at most one thread-

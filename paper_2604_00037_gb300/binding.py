@@ -39,7 +39,7 @@ class AciOpts(C.Structure):
     _fields_ = [("tol_kind", C.c_int32), ("max_sweeps", C.c_int32), ("pivot_mode", C.c_int32),
                 ("precision", C.c_int32), ("seed", C.c_uint64), ("init", C.POINTER(AciTT)),
                 ("out_memory", C.c_int32), ("profile", C.c_int32), ("batch_streams", C.c_int32),
-                ("_pad2", C.c_int32)]
+                ("sweep_overlap", C.c_int32)]
 
 
 class AciStats(C.Structure):
@@ -53,6 +53,7 @@ class AciStats(C.Structure):
 
 KERNEL_CLASSES = ("frame", "pi", "pivot", "other")
 
+OVERLAP_MODES = {"auto": 0, "off": 1, "on": 2}
 PIVOT_MODES = {"full": 0, "rook": 1, "proposed": 2}
 PROPOSER_FEATURES = 7
 
@@ -248,10 +249,11 @@ class Context:
     # ------------------------------------------------------------ the method
     def elementwise(self, a, b=None, op="mul", tol=1e-10, max_rank=64, *, tol_kind="rel",
                     max_sweeps=20, seed=0, init=None, coef=None, out_memory="device",
-                    pivots=False, profile=False, precision="fp64", pivot_mode="full"):
+                    pivots=False, profile=False, precision="fp64", pivot_mode="full", overlap="auto"):
         """y ~ f(a, b) by ACI. ``a``/``b``: lists of cores (torch CUDA tensors, or numpy arrays
         for host memory). ``precision``: "fp64" or "bf16xS" (S = 2..8 digit planes) for the
-        frame and Pi contractions. Returns (cores, stats dict)."""
+        frame and Pi contractions. ``overlap``: "auto", "off" or "on" (aci_overlap, the schedule
+        of the sweeps). Returns (cores, stats dict)."""
         import torch
         A = _TTArg(a)
         Bt = _TTArg(b) if b is not None else None
@@ -264,6 +266,7 @@ class Context:
         opts.profile = 1 if profile else 0
         opts.precision = _precision_code(precision)
         opts.pivot_mode = PIVOT_MODES[pivot_mode]
+        opts.sweep_overlap = OVERLAP_MODES[overlap]
         It = None
         if init is not None:
             It = _TTArg(init)
@@ -328,7 +331,7 @@ class Context:
                              for i, k in enumerate(KERNEL_CLASSES)})
 
     def elementwise_batch(self, items, *, tol_kind="rel", max_sweeps=20, seed=0, out_memory="device",
-                          precision="fp64", pivot_mode="full", streams=0, profile=False):
+                          precision="fp64", pivot_mode="full", streams=0, profile=False, overlap="auto"):
         """Independent products in one call. ``items``: list of dicts with keys a, b (None for
         abs2_mul), op, tol, max_rank (and optional coef). Returns a list of (cores, info) with
         info["status"] per product; raises only for call-level errors."""
@@ -350,6 +353,7 @@ class Context:
         opts.precision = _precision_code(precision)
         opts.pivot_mode = PIVOT_MODES[pivot_mode]
         opts.batch_streams = int(streams)
+        opts.sweep_overlap = OVERLAP_MODES[overlap]
         outs = (AciTT * max(n, 1))()
         stats = (AciStats * max(n, 1))()
         keep = []

@@ -49,6 +49,8 @@ struct aci_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> evfree;  // reusable events for per-kernel timing
     std::vector<cudaEvent_t> evall;
+    cudaStream_t side = nullptr;      // second stream of the overlapped sweep (created on first use)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool own_stream = false;          // a batch worker owns its stream
     bool no_coop = false;             // a batch worker: no cooperative grids (others run beside it)
     std::vector<aci_ctx*> workers;    // batch workers (own streams, scratch and graphs)
@@ -178,6 +180,11 @@ struct Run {
     int* psel_rows = nullptr;
     int* psel_cols = nullptr;
     size_t pcand = 1;          // largest mcap + ncap
+    int overlap_opt = ACI_OVERLAP_AUTO;
+    int overlap = 0;           // overlapped schedule (aci_overlap) in effect
+    T* Qb[2] = {nullptr, nullptr};  // half-products over all candidate rows / columns
+    T* Pfull = nullptr;             // Pi over all candidate rows / columns
+    size_t qcap = 1, pfcap = 1;
     // per-kernel-class accounting (aci_kernel_class)
     double kms[4] = {0, 0, 0, 0};
     long long kcount[4] = {0, 0, 0, 0};
@@ -343,6 +350,10 @@ struct Run {
             psel_rows = c.take<int>(pcand);
             psel_cols = c.take<int>(pcand);
         }
+        if (overlap) {
+            for (int n = 0; n < N; ++n) Qb[n] = c.take<T>(qcap);
+            Pfull = c.take<T>(pfcap);
+        }
         Yptr_dev = c.take<T*>(L);
         pcol_dev = c.take<int*>(std::max(nb, 1));
         jprev_dev = c.take<int*>(std::max(nb, 1));
@@ -406,16 +417,46 @@ struct Run {
         for (int n = 0; n < N; ++n)
             for (int s = 0; s <= L; ++s) rmax = std::max(rmax, r[n][s]);
         for (int s = 0; s <= L; ++s) rmax = std::max(rmax, ry[s]);
-        auto need = [&](int Mm, int Nm, int nprod, int combine) {
-            gpart_elems = std::max(gpart_elems, aci::gemm_part_elems(Mm, Nm, nprod, combine, ctx->num_sms));
-            gcount_n = std::max(gcount_n, aci::gemm_tile_counters(Mm, Nm, nprod));
+        // optional: a contraction of the overlapped schedule, which falls back to the plain one
+        auto need = [&](int Mm, int Nm, int nprod, int combine, bool optional = false) {
             if (digits) {  // K of every contraction is an input rank or an initial-guess rank
                 const aci::TcPlan p = aci::tc_plan(digits, is_cplx, Mm, Nm, rmax, nprod, combine);
-                if (!p.ok) fail(ctx, ACI_E_SHAPE, "contraction too large for the digit-plane precision");
+                if (!p.ok) {
+                    if (optional) {
+                        overlap = 0;
+                        return;
+                    }
+                    fail(ctx, ACI_E_SHAPE, "contraction too large for the digit-plane precision");
+                }
                 tc_bytes = std::max(tc_bytes, aci::tc_scratch_bytes(p));
             }
+            gpart_elems = std::max(gpart_elems, aci::gemm_part_elems(Mm, Nm, nprod, combine, ctx->num_sms));
+            gcount_n = std::max(gcount_n, aci::gemm_tile_counters(Mm, Nm, nprod));
         };
         const int dmax = *std::max_element(d.begin(), d.end());
+        overlap = 0;
+        if (overlap_opt != ACI_OVERLAP_OFF && nb >= 2 && !proposed && !recording &&
+            (overlap_opt == ACI_OVERLAP_ON || (dmax == 2 && !no_coop)))
+            overlap = 1;
+        if (overlap) {  // the contractions of side_lr / side_rl and their buffers
+            qcap = pfcap = 1;
+            const long long lim = 1LL << 31;
+            for (int b = 1; b < nb; ++b) {
+                const long long rows = (long long)mcap[b - 1] * d[b];
+                need((int)std::min(rows, lim - 1), ncap[b], N, 1, true);
+                pfcap = std::max<size_t>(pfcap, (size_t)rows * ncap[b]);
+                for (int n = 0; n < N; ++n) qcap = std::max<size_t>(qcap, (size_t)rows * r[n][b + 1]);
+                need(mcap[b - 1], d[b] * rmax, N, 0, true);
+            }
+            for (int b = 0; b + 1 < nb; ++b) {
+                const long long cols = (long long)d[b + 1] * ncap[b + 1];
+                need(mcap[b], (int)std::min(cols, lim - 1), N, 1, true);
+                pfcap = std::max<size_t>(pfcap, (size_t)mcap[b] * cols);
+                for (int n = 0; n < N; ++n) qcap = std::max<size_t>(qcap, (size_t)r[n][b + 1] * cols);
+                need(rmax * d[b + 1], ncap[b + 1], N, 0, true);
+            }
+            if (pfcap >= (size_t)lim || qcap >= (size_t)lim) overlap = 0;
+        }
         for (int b = 0; b < nb; ++b) need(mcap[b], ncap[b], N, 1);
         for (int s = 0; s < L; ++s) {
             need(cap[s], dmax * rmax, N, 0);           // left half-products
@@ -662,6 +703,168 @@ struct Run {
         gemm(g, mmax, cap[s + 1], kmax_of(s + 1), "right_half", ACI_KCLASS_FRAME);
     }
 
+    // ---------------------------------------------------------------- overlapped schedule
+    // Left to right, bond b >= 1 needs the rows prow[b-1] of Q^n_b = LX^n_{b-1} X^n_b (every row
+    // of Pi[b-1], each a d_b x r_{b+1} block) and the same rows of f(Q_b XR_{b+1}): both are
+    // computed on the side stream during the pivot search of bond b-1 and gathered after it.
+    // Right to left, bond b needs the columns pcol[b+1] of X_{b+1} XR_{b+2} (every column of
+    // Pi[b+1], per sigma_{b+1}) and of f(LX_b X_{b+1} XR_{b+2}), likewise.
+    void fork() {  // the side stream waits for the context stream's work so far
+        ck(ctx, cudaEventRecord(ctx->ev_fork, st), "fork");
+        ck(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0), "fork");
+    }
+    void join() {  // the context stream waits for the side stream's work so far
+        ck(ctx, cudaEventRecord(ctx->ev_join, ctx->side), "join");
+        ck(ctx, cudaStreamWaitEvent(st, ctx->ev_join, 0), "join");
+    }
+    struct OnSide {  // launches (and their timing events) go to the side stream while alive
+        Run* r;
+        cudaStream_t keep;
+        explicit OnSide(Run* rr) : r(rr), keep(rr->st) { r->st = r->ctx->side; }
+        ~OnSide() { r->st = keep; }
+    };
+
+    // Q^n_{b} over every row of Pi[b-1], then Pfull = f(Q_b XR_{b+1}) (rows: Pi[b-1] rows x d_b).
+    void side_lr(int b) {
+        OnSide on(this);
+        aci::GemmArgs<T> g = gemm_base();
+        g.combine = 0;
+        g.nprod = N;
+        int nmax = 1;
+        for (int n = 0; n < N; ++n) {
+            g.A[n] = (b - 1 == 0) ? Xp(n, 0) : LX[n][b - 1];
+            g.B[n] = Xp(n, b);
+            g.C[n] = Qb[n];
+            g.M[n] = dimr(d[b - 1], b - 1);
+            g.N[n] = dimc(d[b] * r[n][b + 1]);
+            g.K[n] = dimc(r[n][b]);
+            g.lda[n] = dimc(r[n][b]);
+            g.ldb[n] = dimc(d[b] * r[n][b + 1]);
+            nmax = std::max(nmax, d[b] * r[n][b + 1]);
+        }
+        gemm(g, mcap[b - 1], nmax, kmax_of(b), "left_half (all rows)", ACI_KCLASS_FRAME);
+        aci::GemmArgs<T> p = gemm_base();
+        p.combine = 1;
+        p.nprod = N;
+        for (int n = 0; n < N; ++n) {
+            p.A[n] = Qb[n];
+            p.B[n] = (b + 1 == L - 1) ? Xp(n, L - 1) : XR[n][b + 1];
+            p.K[n] = dimc(r[n][b + 1]);
+            p.lda[n] = dimc(r[n][b + 1]);
+            p.ldb[n] = dimr(d[b + 1], b + 2);
+        }
+        p.M[0] = dimr(d[b - 1] * d[b], b - 1);
+        p.N[0] = dimr(d[b + 1], b + 2);
+        p.C[0] = Pfull;
+        gemm(p, mcap[b - 1] * d[b], ncap[b], kmax_of(b + 1), "pi_block (all rows)", ACI_KCLASS_PI);
+    }
+
+    // P^n = X^n_{b+1} XR^n_{b+2} over every column of Pi[b+1], then Pfull = f(LX_b P).
+    void side_rl(int b) {
+        OnSide on(this);
+        aci::GemmArgs<T> g = gemm_base();
+        g.combine = 0;
+        g.nprod = N;
+        int mmax = 1;
+        for (int n = 0; n < N; ++n) {
+            g.A[n] = Xp(n, b + 1);
+            g.B[n] = (b + 2 == L - 1) ? Xp(n, L - 1) : XR[n][b + 2];
+            g.C[n] = Qb[n];
+            g.M[n] = dimc(r[n][b + 1] * d[b + 1]);
+            g.N[n] = dimr(d[b + 2], b + 3);
+            g.K[n] = dimc(r[n][b + 2]);
+            g.lda[n] = dimc(r[n][b + 2]);
+            g.ldb[n] = dimr(d[b + 2], b + 3);
+            mmax = std::max(mmax, r[n][b + 1] * d[b + 1]);
+        }
+        gemm(g, mmax, ncap[b + 1], kmax_of(b + 2), "right_half (all columns)", ACI_KCLASS_FRAME);
+        aci::GemmArgs<T> p = gemm_base();
+        p.combine = 1;
+        p.nprod = N;
+        for (int n = 0; n < N; ++n) {
+            p.A[n] = (b == 0) ? Xp(n, 0) : LX[n][b];
+            p.B[n] = Qb[n];
+            p.K[n] = dimc(r[n][b + 1]);
+            p.lda[n] = dimc(r[n][b + 1]);
+            p.ldb[n] = dimr(d[b + 1] * d[b + 2], b + 3);
+        }
+        p.M[0] = dimr(d[b], b);
+        p.N[0] = dimr(d[b + 1] * d[b + 2], b + 3);
+        p.C[0] = Pfull;
+        gemm(p, mcap[b], d[b + 1] * ncap[b + 1], kmax_of(b + 1), "pi_block (all columns)", ACI_KCLASS_PI);
+    }
+
+    // Pi[b] and LX^n_b: rows prow[b-1] of Pfull and of Q^n_b; max |Pi[b]| into the running max.
+    void gather_lr(int b) {
+        aci::GatherArgs<T> a;
+        std::memset(&a, 0, sizeof(a));
+        a.chi = chi;
+        a.smax = smax;
+        a.smax_job = 0;
+        a.njobs = 1 + N;
+        aci::GatherJob<T>& pj = a.job[0];
+        pj.src = Pfull;
+        pj.dst = Pi[b];
+        pj.rows = dimr(d[b], b);
+        pj.cols = pj.sld = pj.dld = dimr(d[b + 1], b + 2);
+        pj.ridx = prow[b - 1];
+        pj.rblk = d[b];
+        long long mx = (long long)mcap[b] * ncap[b];
+        for (int n = 0; n < N; ++n) {
+            aci::GatherJob<T>& j = a.job[1 + n];
+            j.src = Qb[n];
+            j.dst = LX[n][b];
+            j.rows = dimr(1, b);
+            j.cols = j.sld = j.dld = dimc(d[b] * r[n][b + 1]);
+            j.ridx = prow[b - 1];
+            mx = std::max(mx, (long long)cap[b] * d[b] * r[n][b + 1]);
+        }
+        cudaEvent_t e = pre(ACI_KCLASS_OTHER);
+        aci::launch_gather<T>(a, mx, ctx->num_sms, st);
+        post(ACI_KCLASS_OTHER, e, "gather (left to right)");
+    }
+
+    // Pi[b] and XR^n_{b+1}: columns pcol[b+1] (per sigma_{b+1}) of Pfull and of P^n.
+    void gather_rl(int b) {
+        aci::GatherArgs<T> a;
+        std::memset(&a, 0, sizeof(a));
+        a.chi = chi;
+        a.smax = smax;
+        a.smax_job = 0;
+        a.njobs = 1 + N;
+        auto cols_of = [&](aci::GatherJob<T>& j) {
+            j.cols = j.dld = dimr(d[b + 1], b + 2);
+            j.sld = dimr(d[b + 1] * d[b + 2], b + 3);
+            j.cidx = pcol[b + 1];
+            j.cblk = dimr(1, b + 2);
+            j.cstride = dimr(d[b + 2], b + 3);
+        };
+        aci::GatherJob<T>& pj = a.job[0];
+        pj.src = Pfull;
+        pj.dst = Pi[b];
+        pj.rows = dimr(d[b], b);
+        cols_of(pj);
+        long long mx = (long long)mcap[b] * ncap[b];
+        for (int n = 0; n < N; ++n) {
+            aci::GatherJob<T>& j = a.job[1 + n];
+            j.src = Qb[n];
+            j.dst = XR[n][b + 1];
+            j.rows = dimc(r[n][b + 1]);
+            cols_of(j);
+            mx = std::max(mx, (long long)r[n][b + 1] * ncap[b]);
+        }
+        cudaEvent_t e = pre(ACI_KCLASS_OTHER);
+        aci::launch_gather<T>(a, mx, ctx->num_sms, st);
+        post(ACI_KCLASS_OTHER, e, "gather (right to left)");
+    }
+
+    void ensure_side() {
+        if (ctx->side) return;
+        ck(ctx, cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking), "side stream");
+        ck(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "event");
+        ck(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "event");
+    }
+
     // ---------------------------------------------------------------- Algorithm 1
     aci_status run(aci_tt* out, aci_stats* stats, int out_memory) {
         plan_sizes();
@@ -801,9 +1004,47 @@ struct Run {
         // is enqueued once into a CUDA graph and replayed: every shape is read on the device, so
         // the launches are identical from one iteration to the next. It starts by clearing the
         // pivot-search exchange area, so the tags of its launches are fresh at every replay.
+        if (overlap) ensure_side();
+        auto enqueue_overlapped = [&]() {
+            // left to right: bond 0 directly, then each bond's Pi gathered from the side stream's work
+            pi_block(0);
+            fork();
+            side_lr(1);
+            prrlu(Pi[0], dimr(d[0], 0), dimr(d[1], 2), mcap[0], ncap[0], 1, 0, false, eps_lr, smax);
+            for (int b = 1; b < nb; ++b) {
+                join();
+                gather_lr(b);
+                fork();
+                if (b + 1 < nb) side_lr(b + 1);
+                else side_rl(nb - 2);  // the first right-to-left work needs no new pivot
+                prrlu(Pi[b], dimr(d[b], b), dimr(d[b + 1], b + 2), mcap[b], ncap[b], b + 1, b, false,
+                      eps_lr + b, smax);
+            }
+            // right to left: Pi[nb-1] is the block just factored (its frames have not changed)
+            prrlu(Pi[nb - 1], dimr(d[nb - 1], nb - 1), dimr(d[nb], nb + 1), mcap[nb - 1], ncap[nb - 1], nb, nb - 1,
+                  true, eps_rl + nb - 1, smax);
+            for (int b = nb - 2; b >= 0; --b) {
+                join();
+                gather_rl(b);
+                if (b > 0) {
+                    fork();
+                    side_rl(b - 1);
+                }
+                prrlu(Pi[b], dimr(d[b], b), dimr(d[b + 1], b + 2), mcap[b], ncap[b], b + 1, b, true,
+                      eps_rl + b, smax);
+            }
+        };
         auto enqueue_iteration = [&]() {
             ck(ctx, cudaMemsetAsync(ll, 0, ll_words * sizeof(unsigned long long), st), "clear exchange");
             prrlu_launches = 0;
+            if (overlap) {
+                enqueue_overlapped();
+                cudaEvent_t e = pre(ACI_KCLASS_OTHER);
+                aci::launch_iter_check(L, chi, chi_prev, pcol_dev, jprev_dev, eps_lr, eps_rl, smax, err, flags, 0, st);
+                post(ACI_KCLASS_OTHER, e, "iter_check");
+                ck(ctx, cudaMemcpyAsync(ctx->hflags, flags, sizeof(aci::IterFlags), cudaMemcpyDeviceToHost, st), "flags");
+                return;
+            }
             for (int b = 0; b < nb; ++b) {  // left to right, CI "right"
                 left_half(b);
                 if (proposed) {  // the learned restriction; the full right-to-left sweep stays the judge
@@ -1046,6 +1287,7 @@ aci_status run_typed(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, 
     R.rook = o.pivot_mode == ACI_PIVOT_ROOK ? 1 : 0;
     R.no_coop = ctx->no_coop ? 1 : 0;
     R.proposed = o.pivot_mode == ACI_PIVOT_PROPOSED ? 1 : 0;
+    R.overlap_opt = o.sweep_overlap;
     R.recording = ctx->rec_buf != nullptr && !R.proposed;
     if (R.proposed && !ctx->prop_params) fail(ctx, ACI_E_ARG, "ACI_PIVOT_PROPOSED needs aci_set_proposer");
     R.seed = o.seed;
@@ -1102,6 +1344,9 @@ void aci_destroy(aci_ctx* ctx) {
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->evall) cudaEventDestroy(e);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -1137,6 +1382,8 @@ aci_status aci_elementwise_ex(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, ac
         if (o.pivot_mode != ACI_PIVOT_FULL && o.pivot_mode != ACI_PIVOT_ROOK && o.pivot_mode != ACI_PIVOT_PROPOSED)
             fail(ctx, ACI_E_ARG, "unsupported pivot mode");
         if (!valid_precision(o.precision)) fail(ctx, ACI_E_ARG, "unsupported precision");
+        if (o.sweep_overlap < ACI_OVERLAP_AUTO || o.sweep_overlap > ACI_OVERLAP_ON)
+            fail(ctx, ACI_E_ARG, "unsupported sweep_overlap");
         if (o.out_memory != ACI_MEM_DEVICE && o.out_memory != ACI_MEM_HOST) fail(ctx, ACI_E_ARG, "bad out_memory");
         validate_tt(ctx, a, "a");
         const bool unary = op.kind == ACI_OP_ABS2_MUL;

@@ -136,6 +136,19 @@ __host__ __device__ inline DimE dimc(int v) { DimE e; e.mul = v; e.idx = -1; ret
 __host__ __device__ inline DimE dimr(int mul, int idx) { DimE e; e.mul = mul; e.idx = idx; return e; }
 __device__ __forceinline__ int dimv(DimE e, const int* chi) { return e.idx >= 0 ? e.mul * chi[e.idx] : e.mul; }
 
+// Index maps of the gathers. Row r: none (idx NULL), plain (blk 0: idx[r]) or by blocks of blk
+// rows (idx[r / blk] * blk + r % blk: rows idx of a matrix whose rows are blk rows long each).
+// Column c: none, plain (blk 0: idx[c]) or by blocks of blk columns, each block taken from a slab
+// of `stride` source columns (c / blk * stride + idx[c % blk]).
+__device__ __forceinline__ int gather_row(const int* idx, int blk, int r) {
+    if (!idx) return r;
+    return blk > 0 ? idx[r / blk] * blk + r % blk : idx[r];
+}
+__device__ __forceinline__ int gather_col(const int* idx, int blk, int stride, int c) {
+    if (!idx) return c;
+    return blk > 0 ? (c / blk) * stride + idx[c % blk] : idx[c];
+}
+
 // Error flags raised by kernels and read by the host once per sweep.
 enum DevErr { DEVERR_TIMEOUT = 1, DEVERR_NUMERIC = 2 };
 

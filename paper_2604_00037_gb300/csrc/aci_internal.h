@@ -214,6 +214,28 @@ struct IterFlags {
     double emax;
     double S;
 };
+// Gathers of the overlapped sweep: dst[r * dld + c] = src[gather_row(r) * sld + gather_col(c)]
+// for r < rows, c < cols (shapes read on the device), up to three independent jobs per launch.
+// One job may also fold max |dst| into *smax (bits of a non-negative double, as the contractions).
+template <class T> struct GatherJob {
+    const T* src;
+    T* dst;
+    DimE rows, cols, sld, dld;
+    const int* ridx;  // see gather_row
+    int rblk;
+    const int* cidx;  // see gather_col
+    DimE cblk, cstride;
+};
+constexpr int kGatherJobs = 3;
+template <class T> struct GatherArgs {
+    GatherJob<T> job[kGatherJobs];
+    int njobs;
+    int smax_job;  // job whose values feed smax, -1 for none
+    const int* chi;
+    unsigned long long* smax;
+};
+template <class T> void launch_gather(const GatherArgs<T>& a, long long max_elems, int num_sms, cudaStream_t st);
+
 void launch_iter_check(int L, const int* chi, int* chi_prev, int* const* pcol, int* const* jprev,
                        const double* eps_lr, const double* eps_rl, const unsigned long long* smax,
                        const int* err, IterFlags* flags, int snapshot_only, cudaStream_t st);

@@ -1,5 +1,7 @@
 // Output assembly (CI-canonical form, Eq. (ycicanonical): Y_l = T_l P_l^-1), the random
 // initial guess of Algorithm 1, and the end-of-iteration test of Algorithm 1.
+#include <algorithm>
+
 #include "aci_internal.h"
 
 namespace aci {
@@ -149,7 +151,44 @@ __global__ void iter_check_kernel(int L, const int* chi, int* chi_prev, int* con
     }
 }
 
+// ---------------------------------------------------------------- gathers of the overlapped sweep
+template <class T>
+__global__ void __launch_bounds__(256) gather_kernel(GatherArgs<T> a) {
+    const GatherJob<T>& j = a.job[blockIdx.y];
+    const int rows = dimv(j.rows, a.chi), cols = dimv(j.cols, a.chi);
+    const int sld = dimv(j.sld, a.chi), dld = dimv(j.dld, a.chi);
+    const int cblk = j.cblk.mul ? dimv(j.cblk, a.chi) : 0;
+    const int cstride = j.cblk.mul ? dimv(j.cstride, a.chi) : 0;
+    const long long n = (long long)rows * cols;
+    unsigned long long mk = 0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / cols), c = (int)(e - (long long)r * cols);
+        const T v = j.src[(size_t)gather_row(j.ridx, j.rblk, r) * sld + gather_col(j.cidx, cblk, cstride, c)];
+        j.dst[(size_t)r * dld + c] = v;
+        const unsigned long long k = key_of(v);
+        mk = k > mk ? k : mk;
+    }
+    if (a.smax && (int)blockIdx.y == a.smax_job) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long ov = __shfl_xor_sync(0xffffffffu, mk, off);
+            mk = ov > mk ? ov : mk;
+        }
+        if ((threadIdx.x & 31) == 0 && mk) {
+            const double mag = key_to_mag(__longlong_as_double((long long)mk), T());
+            atomicMax(a.smax, (unsigned long long)__double_as_longlong(mag));
+        }
+    }
+}
+
 }  // namespace
+
+template <class T>
+void launch_gather(const GatherArgs<T>& a, long long max_elems, int num_sms, cudaStream_t st) {
+    const long long want = (max_elems + 1023) / 1024;
+    const int bx = (int)std::max(1LL, std::min(want, (long long)num_sms * 4));
+    gather_kernel<T><<<dim3(bx, a.njobs), 256, 0, st>>>(a);
+}
 
 template <class T>
 void launch_assemble(const AssembleArgs<T>& a, int Rmax, cudaStream_t st) {
@@ -185,6 +224,8 @@ void launch_iter_check(int L, const int* chi, int* chi_prev, int* const* pcol, i
                                          flags, snapshot_only);
 }
 
+template void launch_gather<double>(const GatherArgs<double>&, long long, int, cudaStream_t);
+template void launch_gather<cplx>(const GatherArgs<cplx>&, long long, int, cudaStream_t);
 template void launch_assemble<double>(const AssembleArgs<double>&, int, cudaStream_t);
 template void launch_assemble<cplx>(const AssembleArgs<cplx>&, int, cudaStream_t);
 template void launch_apply_pinv<double>(const double*, int, int, const double*, const double*,

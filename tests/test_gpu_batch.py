@@ -49,15 +49,17 @@ def same(x, y):
     return len(x) == len(y) and all(torch.equal(p, q) for p, q in zip(x, y))
 
 
-@pytest.mark.parametrize("streams", [1, 3, 0])
-def test_batch_equals_single_calls(ctx, streams):
+@pytest.mark.parametrize("streams,overlap", [(1, "auto"), (3, "auto"), (0, "auto"), (3, "on")])
+def test_batch_equals_single_calls(ctx, streams, overlap):
+    """In a batch the automatic schedule is the plain one; an explicit schedule is kept."""
     items = make_items(1, 9)
     res = ctx.elementwise_batch([dict(it, a=dev(it["a"]), b=dev(it["b"]) if it["b"] is not None else None)
-                                 for it in items], streams=streams)
+                                 for it in items], streams=streams, overlap=overlap)
+    single = "off" if overlap == "auto" else overlap
     for it, (cores, info) in zip(items, res):
         assert info["status"] in ("ACI_OK", "ACI_W_NOT_CONVERGED")
         ins = [dev(it["a"])] + ([dev(it["b"])] if it["b"] is not None else [None])
-        ref, rinfo = ctx.elementwise(*ins, op=it["op"], tol=it["tol"], max_rank=it["max_rank"])
+        ref, rinfo = ctx.elementwise(*ins, op=it["op"], tol=it["tol"], max_rank=it["max_rank"], overlap=single)
         assert same(cores, ref)
         assert info["ranks"] == rinfo["ranks"] and info["iterations"] == rinfo["iterations"]
 
