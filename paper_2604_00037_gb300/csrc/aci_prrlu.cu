@@ -664,6 +664,26 @@ __device__ __forceinline__ void warp_best(kbits_t& k, int& l, T& v, int& s) {
     s = __shfl_sync(0xffffffffu, s, src);
 }
 
+// Positions of the register-resident kernel: (row << 16) | column. For column < n <= 65536 they
+// order like row * n + column, so the lowest-position tie-break is unchanged, and they decode
+// with shifts instead of integer divisions on the step's critical path.
+__device__ __forceinline__ int cpos(int r, int c) { return (r << 16) + c; }
+__device__ __forceinline__ int cpos_row(int p) { return p >> 16; }
+__device__ __forceinline__ int cpos_col(int p) { return p & 0xFFFF; }
+
+// v[j] for a runtime j in [0, W) by a tree of selects (log2 W levels instead of a chain of W).
+template <class T, int W>
+__device__ __forceinline__ T select_reg(const T (&v)[W], int j) {
+    T t[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) t[c] = v[c];
+#pragma unroll
+    for (int s = 1; s < W; s <<= 1)
+#pragma unroll
+        for (int c = 0; c + s < W; c += 2 * s) t[c] = (j & s) ? t[c + s] : t[c];
+    return t[0];
+}
+
 template <class T, int ROWS, int WMAX>
 __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
     namespace cg = cooperative_groups;
@@ -700,7 +720,8 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
             if (live[i] && cc < w) {
                 x = src[cc];
                 const kbits_t k = key_of(x);
-                if (better(k, r * n + c0 + cc, bkey, blin)) { bkey = k; blin = r * n + c0 + cc; bval = x; }
+                const int pos = cpos(r, c0 + cc);
+                if (better(k, pos, bkey, blin)) { bkey = k; blin = pos; bval = x; }
             }
             v[i][cc] = x;
         }
@@ -729,17 +750,11 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
         T cv = s_zero(T());
         if (lane < RWARP) { ck = wmx[lane].key; cl_ = wmx[lane].lin; cv = wmx[lane].val; }
         warp_best(ck, cl_, cv, cs);
-        const int ccb = (cl_ != INT_MAX) ? (cl_ % n - c0) : -1;
+        const int ccb = (cl_ != INT_MAX) ? (cpos_col(cl_) - c0) : 0;
 #pragma unroll
         for (int i = 0; i < ROWS; ++i) {
             const int r = tid + i * RT;
-            if (r < m) {
-                T x = s_zero(T());
-#pragma unroll
-                for (int cc = 0; cc < WMAX; ++cc)
-                    if (cc == ccb) x = v[i][cc];
-                candcol[(size_t)par * mmax + r] = x;
-            }
+            if (r < m) candcol[(size_t)par * mmax + r] = select_reg<T, WMAX>(v[i], ccb);
         }
         if (warp == 0) {
             Cand<T> mine;
@@ -750,36 +765,28 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
             for (int t = lane; t < C; t += 32) *cl.map_shared_rank(cand + par * C + g, t) = mine;
         }
         cl.sync();
-        // (2) the winner among the C candidates and the step's decision: warp 0 only (the FP64
-        //     work of the decision is latency-bound), read by everyone after one barrier
-        if (warp == 0) {
-            kbits_t wk = 0;
-            int wl = INT_MAX, gw = 0;
-            T pv = s_zero(T());
-            for (int t = lane; t < C; t += 32) {
-                const Cand<T>& c = cand[par * C + t];
-                if (better(c.key, c.lin, wk, wl)) { wk = c.key; wl = c.lin; pv = c.val; gw = t; }
-            }
-            warp_best(wk, wl, pv, gw);
-            if (lane == 0) {
-                decide(dec, wk, wl, pv, p, kmax, tau, false);
-                dec->lin = wl;
-                dec->gw = gw;
-                dec->piv = pv;
-            }
+        // (2) the winner among the C candidates (C <= 32) and the step's decision, taken by every
+        //     warp alike from its own copy of the candidates (integer work, no broadcast barrier)
+        kbits_t wk = 0;
+        int wl = INT_MAX, gw = 0;
+        T pv = s_zero(T());
+        if (lane < C) {
+            const Cand<T>& c = cand[par * C + lane];
+            wk = c.key;
+            wl = c.lin;
+            pv = c.val;
+            gw = lane;
         }
-        __syncthreads();
-        const int code = dec->code;
-        if (code) {
-            if (code == 2 && g == 0 && tid == 0) atomicOr(a.err, DEVERR_NUMERIC);
-            eps = dec->eps;
+        warp_best(wk, wl, pv, gw);
+        Decision<T> dl;
+        decide(&dl, wk, wl, pv, p, kmax, tau, false);
+        if (dl.code) {
+            if (dl.code == 2 && g == 0 && tid == 0) atomicOr(a.err, DEVERR_NUMERIC);
+            eps = dl.eps;
             break;
         }
-        const int zpiv = dec->zpiv;
-        const T pv = dec->piv;
-        const int gw = dec->gw;
-        const int wl = dec->lin;
-        const int ri = wl / n, cj = wl % n;
+        const int zpiv = dl.zpiv;
+        const int ri = cpos_row(wl), cj = cpos_col(wl);
         if (g == 0 && tid == 0) {
             a.piv_rows[p] = ri;
             a.piv_cols[p] = cj;
@@ -828,7 +835,7 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
 #pragma unroll
         for (int i = 0; i < ROWS; ++i) {
             if (!live[i]) continue;
-            const int rn = (tid + i * RT) * n + c0;
+            const int rn = cpos(tid + i * RT, c0);
 #pragma unroll
             for (int cc = 0; cc < WMAX; ++cc) {
                 if ((colmask >> cc) & 1u) {
