@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--proposer", action="store_true",
                     help="the learned-proposal sequence: train on steps 0-39, compare on 40-59")
     ap.add_argument("--seq-steps", type=int, default=60)
-    ap.add_argument("--keep", type=float, default=1.25)
+    ap.add_argument("--keep", default="1.25",
+                    help="proposer: kept candidates per side = keep x previous rank + 8; a comma list compares several")
     return ap.parse_args()
 
 
@@ -116,21 +117,23 @@ def run_proposer(args):
     print(f"proposer: {X.shape[0]} records ({pos:.3f} positive), loss {loss:.4f}, {train_s:.1f} s", file=sys.stderr,
           flush=True)
     rng = np.random.default_rng(8)
-    rows = {"plain": [], "proposed": []}
+    keeps = [float(k) for k in str(args.keep).split(",")]
+    modes = ["plain"] + ["proposed" if i == 0 else f"proposed@{k:g}" for i, k in enumerate(keeps)]
+    rows = {m: [] for m in modes}
     for t in range(ntrain, nsteps):
         a, b = pairs[t]
         pts = rng.integers(0, 2, size=(20000, len(a)))
         exact = tt_eval(a, pts) * tt_eval(b, pts)
         A, B = dev(a), dev(b)
-        for mode in ("plain", "proposed"):
-            if mode == "proposed":
-                ctx.set_proposer(P, keep=args.keep)
+        for mi, mode in enumerate(modes):
+            if mode != "plain":
+                ctx.set_proposer(P, keep=keeps[mi - 1])
             for rep in range(2):  # the second run is timed
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 ycores, info = ctx.elementwise(A, B, "mul", tol, max_rank, max_sweeps=args.max_sweeps,
-                                               pivot_mode="proposed" if mode == "proposed" else "full")
+                                               pivot_mode="full" if mode == "plain" else "proposed")
                 e1.record()
                 torch.cuda.synchronize()
             yv = tt_eval([c.cpu().numpy() for c in ycores], pts)
@@ -161,8 +164,10 @@ def run_proposer(args):
                        "keep": args.keep, "input_generation_s": gen_s},
             "training": {"records": int(X.shape[0]), "positive_share": pos, "final_loss": loss,
                          "adam_steps": 400, "train_s": train_s},
-            "plain": summ["plain"], "proposed": summ["proposed"],
+            **{m: summ[m] for m in modes},
             "speedup": summ["plain"]["ms_per_product"] / summ["proposed"]["ms_per_product"],
+            **{f"speedup@{k:g}": summ["plain"]["ms_per_product"] / summ[m]["ms_per_product"]
+               for k, m in zip(keeps, modes[1:])},
             "held_out_auc": float((zp[:, None] > zn[None, :]).mean()) if len(zp) and len(zn) else float("nan")}
     print(json.dumps(line), flush=True)
     ctx.close()

@@ -130,13 +130,13 @@ typedef struct {
  * a second stream while the previous bond's pivot search runs, then gathers the selected ones:
  * d_b times the contraction work, taken off the critical path of the sweep. Results differ from
  * the plain schedule only by the rounding of the contractions (their K splits differ).
- *  ACI_OVERLAP_AUTO  overlapped when every local dimension is 2 and the call is neither a
- *                    learned-proposal call (ACI_PIVOT_PROPOSED) nor recording proposer data,
- *                    nor one product of aci_elementwise_batch (whose products already fill the
- *                    GPU); plain otherwise
+ *  ACI_OVERLAP_AUTO  overlapped when every local dimension is 2 and the call is not one product
+ *                    of aci_elementwise_batch (whose products already fill the GPU); plain
+ *                    otherwise
  *  ACI_OVERLAP_OFF   plain: every step on the context stream, in order
- *  ACI_OVERLAP_ON    overlapped wherever it applies (L >= 3; not with ACI_PIVOT_PROPOSED or
- *                    recording, which keep the plain left-to-right sweep)                    */
+ *  ACI_OVERLAP_ON    overlapped wherever it applies (L >= 3)
+ * With ACI_PIVOT_PROPOSED only the right-to-left sweep (the full one) is overlapped; the learned
+ * left-to-right sweep keeps the plain order.                                                   */
 typedef enum { ACI_OVERLAP_AUTO = 0, ACI_OVERLAP_OFF = 1, ACI_OVERLAP_ON = 2 } aci_overlap;
 
 /* Kernel classes of aci_stats.kernel_* (profile = 1). Flops are real-equivalent (a complex

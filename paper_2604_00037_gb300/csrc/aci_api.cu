@@ -14,6 +14,7 @@
 // sweep is reused by the following right-to-left sweep at the same bond, and XR[.][b+1] from a
 // right-to-left sweep by the next left-to-right sweep (their frames have not changed).
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -179,6 +180,7 @@ struct Run {
     float* pscore = nullptr;   // proposer scores
     int* psel_rows = nullptr;
     int* psel_cols = nullptr;
+    int* pside = nullptr;      // [4] side maxima of the proposer's norm features
     size_t pcand = 1;          // largest mcap + ncap
     int overlap_opt = ACI_OVERLAP_AUTO;
     int overlap = 0;           // overlapped schedule (aci_overlap) in effect
@@ -349,6 +351,7 @@ struct Run {
             pscore = c.take<float>(pcand);
             psel_rows = c.take<int>(pcand);
             psel_cols = c.take<int>(pcand);
+            pside = c.take<int>(4);
         }
         if (overlap) {
             for (int n = 0; n < N; ++n) Qb[n] = c.take<T>(qcap);
@@ -435,8 +438,7 @@ struct Run {
         };
         const int dmax = *std::max_element(d.begin(), d.end());
         overlap = 0;
-        if (overlap_opt != ACI_OVERLAP_OFF && nb >= 2 && !proposed && !recording &&
-            (overlap_opt == ACI_OVERLAP_ON || (dmax == 2 && !no_coop)))
+        if (overlap_opt != ACI_OVERLAP_OFF && nb >= 2 && (overlap_opt == ACI_OVERLAP_ON || (dmax == 2 && !no_coop)))
             overlap = 1;
         if (overlap) {  // the contractions of side_lr / side_rl and their buffers
             qcap = pfcap = 1;
@@ -590,7 +592,10 @@ struct Run {
         a.mcap = mcap[b];
         a.ncap = ncap[b];
         cudaEvent_t e = pre(ACI_KCLASS_OTHER);
-        aci::launch_features<T>(a, st);
+        a.side_max = pside;
+        aci::launch_features<T>(a, ctx->num_sms, st);
+        ctx->launches++;  // the norm pass and the finishing pass
+        kcount[ACI_KCLASS_OTHER]++;
         post(ACI_KCLASS_OTHER, e, "proposer features");
     }
 
@@ -901,6 +906,10 @@ struct Run {
         ck(ctx, cudaMemsetAsync(ll, 0, ll_words * sizeof(unsigned long long), st), "clear exchange");
         prrlu_launches = 0;
         ck(ctx, cudaMemsetAsync(gcount, 0, gcount_n * sizeof(int), st), "clear counters");
+        if (pside) {  // the features' side maxima start empty; every features call leaves them so
+            static const int kEmpty[4] = {INT_MIN, INT_MIN, INT_MIN, INT_MIN};
+            ck(ctx, cudaMemcpyAsync(pside, kEmpty, sizeof(kEmpty), cudaMemcpyHostToDevice, st), "init side maxima");
+        }
         T one_h;
         std::memset(&one_h, 0, sizeof(T));
         *reinterpret_cast<double*>(&one_h) = 1.0;
@@ -1006,21 +1015,37 @@ struct Run {
         // pivot-search exchange area, so the tags of its launches are fresh at every replay.
         if (overlap) ensure_side();
         auto enqueue_overlapped = [&]() {
-            // left to right: bond 0 directly, then each bond's Pi gathered from the side stream's work
-            pi_block(0);
-            fork();
-            side_lr(1);
-            prrlu(Pi[0], dimr(d[0], 0), dimr(d[1], 2), mcap[0], ncap[0], 1, 0, false, eps_lr, smax);
-            for (int b = 1; b < nb; ++b) {
-                join();
-                gather_lr(b);
+            if (proposed) {
+                // the learned restriction keeps the plain left-to-right sweep; its last Pi block
+                // is restricted, so the right-to-left sweep starts from the full block
+                for (int b = 0; b < nb; ++b) {
+                    left_half(b);
+                    proposed_update(b);
+                }
+                pi_block(nb - 1);
                 fork();
-                if (b + 1 < nb) side_lr(b + 1);
-                else side_rl(nb - 2);  // the first right-to-left work needs no new pivot
-                prrlu(Pi[b], dimr(d[b], b), dimr(d[b + 1], b + 2), mcap[b], ncap[b], b + 1, b, false,
-                      eps_lr + b, smax);
+                side_rl(nb - 2);
+            } else {
+                // left to right: bond 0 directly, then each bond's Pi gathered from the side stream's work
+                pi_block(0);
+                fork();
+                side_lr(1);
+                if (recording) features(0);
+                prrlu(Pi[0], dimr(d[0], 0), dimr(d[1], 2), mcap[0], ncap[0], 1, 0, false, eps_lr, smax);
+                if (recording) record(0);
+                for (int b = 1; b < nb; ++b) {
+                    join();
+                    gather_lr(b);
+                    fork();
+                    if (b + 1 < nb) side_lr(b + 1);
+                    else side_rl(nb - 2);  // the first right-to-left work needs no new pivot
+                    if (recording) features(b);
+                    prrlu(Pi[b], dimr(d[b], b), dimr(d[b + 1], b + 2), mcap[b], ncap[b], b + 1, b, false,
+                          eps_lr + b, smax);
+                    if (recording) record(b);
+                }
             }
-            // right to left: Pi[nb-1] is the block just factored (its frames have not changed)
+            // right to left: Pi[nb-1] is the full block of the last bond (its frames have not changed)
             prrlu(Pi[nb - 1], dimr(d[nb - 1], nb - 1), dimr(d[nb], nb + 1), mcap[nb - 1], ncap[nb - 1], nb, nb - 1,
                   true, eps_rl + nb - 1, smax);
             for (int b = nb - 2; b >= 0; --b) {

@@ -10,6 +10,7 @@
 //   2     sigma / (d - 1);  3  alpha / chi (position of the parent pivot);  4  b / (L - 1);
 //   5     1 if the candidate was a pivot of this bond in the previous sweep;  6  1 for columns.
 #include <algorithm>
+#include <climits>
 #include <mutex>
 
 #include "aci_internal.h"
@@ -23,9 +24,68 @@ constexpr int kPT = 1024;
 __device__ __forceinline__ double sq(double v) { return v * v; }
 __device__ __forceinline__ double sq(cplx v) { return v.re * v.re + v.im * v.im; }
 
+// Order-preserving int image of a float (for atomicMax) and its inverse.
+__device__ __forceinline__ int fkey(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float fkey_inv(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7FFFFFFF); }
+
+constexpr int kNT = 256;  // threads of the norm kernel
+
+// Pass 1 over the whole GPU: 0.5 log2 of each candidate's squared norm per input, into features 0
+// and 1 (raw), and the side maxima. Rows: one warp per row (lanes along K, coalesced); columns: one
+// thread per column (threads along the row of B, coalesced).
+template <class T>
+__global__ void __launch_bounds__(kNT) features_norm_kernel(ProposerArgs<T> a, int row_blocks) {
+    const int lane = threadIdx.x & 31;
+    const bool cols = (int)blockIdx.x >= row_blocks;
+    float l2[2] = {-1e30f, -1e30f};
+    int i;
+    bool valid;
+    if (!cols) {
+        i = (int)blockIdx.x * (kNT / 32) + (threadIdx.x >> 5);
+        valid = i < dimv(a.M, a.chi);
+        if (i >= a.mcap) return;  // whole warp
+        for (int q = 0; q < a.nprod; ++q) {
+            double s = 0.0;
+            if (valid) {
+                const int K = dimv(a.K[q], a.chi), lda = dimv(a.lda[q], a.chi);
+                const T* row = a.A[q] + (size_t)i * lda;
+                for (int k = lane; k < K; k += 32) s += sq(row[k]);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            l2[q] = s > 0.0 ? 0.5f * log2f((float)s) : -1e30f;
+        }
+        if (lane != 0) return;
+    } else {
+        i = ((int)blockIdx.x - row_blocks) * kNT + threadIdx.x;
+        if (i >= a.ncap) return;
+        valid = i < dimv(a.N, a.chi);
+        for (int q = 0; q < a.nprod && valid; ++q) {
+            const int K = dimv(a.K[q], a.chi), ldb = dimv(a.ldb[q], a.chi);
+            double s = 0.0;
+            for (int k = 0; k < K; ++k) s += sq(a.B[q][(size_t)k * ldb + i]);
+            l2[q] = s > 0.0 ? 0.5f * log2f((float)s) : -1e30f;
+        }
+    }
+    if (a.nprod == 1) l2[1] = l2[0];
+    float* x = a.X + ((cols ? (size_t)a.mcap : 0) + i) * kPropFeatures;
+    x[0] = l2[0];
+    x[1] = l2[1];
+    if (valid) {
+        atomicMax(a.side_max + (cols ? 2 : 0), fkey(l2[0]));
+        atomicMax(a.side_max + (cols ? 3 : 1), fkey(l2[1]));
+    }
+}
+
+// Pass 2, one CTA per side: features 0 and 1 relative to the side maxima, the others from the
+// candidate's position; resets the side maxima for the next call.
 template <class T>
 __global__ void __launch_bounds__(kPT) features_kernel(ProposerArgs<T> a) {
-    __shared__ float smax[kPT / 32];
+    constexpr int kBits = 1 << 16;  // previous-pivot bitmap (larger sides scan the list instead)
+    __shared__ unsigned int was_bits[kBits / 32];
     const bool cols = blockIdx.x == 1;
     const int live = cols ? dimv(a.N, a.chi) : dimv(a.M, a.chi);
     const int cap = cols ? a.ncap : a.mcap;
@@ -34,43 +94,18 @@ __global__ void __launch_bounds__(kPT) features_kernel(ProposerArgs<T> a) {
     const int kprev = dimv(a.kprev, a.chi);
     const int* prev = cols ? a.prev_cols : a.prev_rows;
     float* X = a.X + (cols ? (size_t)a.mcap * kPropFeatures : 0);
-    float lmax[2] = {-1e30f, -1e30f};
-    // pass 1: log2 norms into the feature rows, side maximum
-    for (int i = threadIdx.x; i < cap; i += kPT) {
-        float l2[2] = {-1e30f, -1e30f};
-        if (i < live) {
-            for (int q = 0; q < a.nprod; ++q) {
-                const int K = dimv(a.K[q], a.chi);
-                double s = 0.0;
-                if (!cols) {
-                    const int lda = dimv(a.lda[q], a.chi);
-                    const T* row = a.A[q] + (size_t)i * lda;
-                    for (int k = 0; k < K; ++k) s += sq(row[k]);
-                } else {
-                    const int ldb = dimv(a.ldb[q], a.chi);
-                    for (int k = 0; k < K; ++k) s += sq(a.B[q][(size_t)k * ldb + i]);
-                }
-                l2[q] = s > 0.0 ? 0.5f * log2f((float)s) : -1e30f;
-            }
-            if (a.nprod == 1) l2[1] = l2[0];
+    int* smx = a.side_max + (cols ? 2 : 0);
+    const float lmax[2] = {fkey_inv(smx[0]), fkey_inv(smx[1])};
+    const bool bitmap = cap <= kBits;
+    if (bitmap) {
+        for (int w = threadIdx.x; w < (cap + 31) / 32; w += kPT) was_bits[w] = 0u;
+        __syncthreads();
+        for (int p = threadIdx.x; p < kprev; p += kPT) {
+            const int r = prev[p];
+            if (r >= 0 && r < cap) atomicOr(&was_bits[r >> 5], 1u << (r & 31));
         }
-        X[(size_t)i * kPropFeatures + 0] = l2[0];
-        X[(size_t)i * kPropFeatures + 1] = l2[1];
-        lmax[0] = fmaxf(lmax[0], l2[0]);
-        lmax[1] = fmaxf(lmax[1], l2[1]);
-    }
-    for (int q = 0; q < 2; ++q) {
-        float v = lmax[q];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
         __syncthreads();
-        if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = v;
-        __syncthreads();
-        float m = -1e30f;
-        for (int w = 0; w < kPT / 32; ++w) m = fmaxf(m, smax[w]);
-        lmax[q] = m;
     }
-    // pass 2: the remaining features
     for (int i = threadIdx.x; i < cap; i += kPT) {
         float* x = X + (size_t)i * kPropFeatures;
         if (i >= live) {
@@ -84,10 +119,16 @@ __global__ void __launch_bounds__(kPT) features_kernel(ProposerArgs<T> a) {
         x[3] = (float)pos / (float)max(chi_side, 1);
         x[4] = a.bond_frac;
         int was = 0;
-        for (int p = 0; p < kprev; ++p) was |= prev[p] == i;
+        if (bitmap) {
+            was = (was_bits[i >> 5] >> (i & 31)) & 1u;
+        } else {
+            for (int p = 0; p < kprev; ++p) was |= prev[p] == i;
+        }
         x[5] = (float)was;
         x[6] = cols ? 1.f : 0.f;
     }
+    __syncthreads();
+    if (threadIdx.x < 2) smx[threadIdx.x] = INT_MIN;
 }
 
 // Keep the K best-scoring live candidates of each side, in ascending index order; K = min(live,
@@ -179,11 +220,15 @@ __global__ void record_kernel(RecordArgs r) {
 }  // namespace
 
 template <class T>
-void launch_features(const ProposerArgs<T>& a, cudaStream_t st) {
+void launch_features(const ProposerArgs<T>& a, int num_sms, cudaStream_t st) {
+    (void)num_sms;
+    const int row_blocks = (a.mcap + kNT / 32 - 1) / (kNT / 32);
+    const int col_blocks = (a.ncap + kNT - 1) / kNT;
+    features_norm_kernel<T><<<row_blocks + col_blocks, kNT, 0, st>>>(a, row_blocks);
     features_kernel<T><<<2, kPT, 0, st>>>(a);
 }
-template void launch_features<double>(const ProposerArgs<double>&, cudaStream_t);
-template void launch_features<cplx>(const ProposerArgs<cplx>&, cudaStream_t);
+template void launch_features<double>(const ProposerArgs<double>&, int, cudaStream_t);
+template void launch_features<cplx>(const ProposerArgs<cplx>&, int, cudaStream_t);
 
 size_t topk_smem(int mcap, int ncap) {
     int P = 1;
