@@ -403,7 +403,8 @@ def source_hash(path):
 
 
 def recorded_traffic(kernel_class):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel source still matches."""
+    """DRAM bytes per byte of the launch's input block, from a committed ncu summary
+    (profiles/traffic.txt: class, source hash, ratio), if the kernel source still matches."""
     f = os.path.join(ROOT, "profiles", "traffic.txt")
     src = {"pivot": "aci_prrlu.cu", "pi": "aci_gemm.cu", "frame": "aci_gemm.cu"}.get(kernel_class)
     if not src or not os.path.exists(f):
@@ -414,6 +415,13 @@ def recorded_traffic(kernel_class):
         if len(parts) >= 3 and parts[0] == kernel_class and parts[1] == h:
             return float(parts[2])
     return None
+
+
+def mean_pi_bytes(ranks, d=2):
+    """Mean bytes of one Π block (FP64) over the bonds at the final ranks: the input block a
+    pivot-search launch reads."""
+    nb = len(ranks) - 2
+    return sum(8.0 * d * ranks[b] * d * ranks[b + 2] for b in range(nb)) / max(nb, 1)
 
 
 def main():
@@ -489,13 +497,17 @@ def main():
     kfl = {c: sum(i["kernels"][c]["flops"] for i in infos) for c in classes}
     dom = max(("frame", "pi", "pivot"), key=lambda c: kms[c])
     achieved = kfl[dom] / (kms[dom] / 1e3) / 1e12
-    traffic = recorded_traffic(dom)
+    ratio = recorded_traffic(dom)
+    traffic = ratio * mean_pi_bytes(infos[-1]["ranks"]) if ratio is not None and dom == "pivot" else None
     roofline = {"bound": "alu", "kernel": {"frame": "gemm_kernel (frame half-products)",
                                            "pi": "gemm_kernel (Pi block + f)",
                                            "pivot": "prrlu_kernel"}[dom],
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": traffic * kcnt[dom] / max(kcnt[dom], 1) if traffic is not None else None,
+                "traffic": traffic,
+                "traffic_note": ("DRAM bytes per launch: the ncu ratio of DRAM bytes to input-block bytes "
+                                 "(profiles/prrlu_creg_kernel_480x480_k240.md) times the mean Π block at the "
+                                 "final ranks" if traffic is not None else "no capture of the current kernel source"),
                 "peak_source": "FP64 vector peak, nominal 1.25 TFLOP/s (no FP64 tensor path on GB300)",
                 "share": kms[dom] / total_ms * (world if world > 1 else 1),
                 "classes_ms_per_step": {c: kms[c] / args.steps for c in classes},
