@@ -593,7 +593,7 @@ struct Run {
         a.ncap = ncap[b];
         cudaEvent_t e = pre(ACI_KCLASS_OTHER);
         a.side_max = pside;
-        aci::launch_features<T>(a, ctx->num_sms, st);
+        aci::launch_features<T>(a, st);
         ctx->launches++;  // the norm pass and the finishing pass
         kcount[ACI_KCLASS_OTHER]++;
         post(ACI_KCLASS_OTHER, e, "proposer features");

@@ -149,7 +149,7 @@ template <class T> struct ProposerArgs {
     int* side_max;        // [4] order-preserving int images of the side maxima of features 0, 1
                           // (rows q = 0, 1, then columns); INT_MIN between calls
 };
-template <class T> void launch_features(const ProposerArgs<T>& a, int num_sms, cudaStream_t st);
+template <class T> void launch_features(const ProposerArgs<T>& a, cudaStream_t st);
 struct TopkArgs {
     const float* z;       // (mcap + ncap) scores
     DimE M, N, kprev;

@@ -220,15 +220,14 @@ __global__ void record_kernel(RecordArgs r) {
 }  // namespace
 
 template <class T>
-void launch_features(const ProposerArgs<T>& a, int num_sms, cudaStream_t st) {
-    (void)num_sms;
+void launch_features(const ProposerArgs<T>& a, cudaStream_t st) {
     const int row_blocks = (a.mcap + kNT / 32 - 1) / (kNT / 32);
     const int col_blocks = (a.ncap + kNT - 1) / kNT;
     features_norm_kernel<T><<<row_blocks + col_blocks, kNT, 0, st>>>(a, row_blocks);
     features_kernel<T><<<2, kPT, 0, st>>>(a);
 }
-template void launch_features<double>(const ProposerArgs<double>&, int, cudaStream_t);
-template void launch_features<cplx>(const ProposerArgs<cplx>&, int, cudaStream_t);
+template void launch_features<double>(const ProposerArgs<double>&, cudaStream_t);
+template void launch_features<cplx>(const ProposerArgs<cplx>&, cudaStream_t);
 
 size_t topk_smem(int mcap, int ncap) {
     int P = 1;
