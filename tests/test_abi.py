@@ -48,3 +48,33 @@ def test_product_path_has_no_cpu_fallback():
     if not torch.cuda.is_available():
         with pytest.raises(RuntimeError):
             pkg.Context(0)
+
+
+def _header():
+    return re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "aci.h")).read(), flags=re.S)
+
+
+def _enum_values(src, prefix):
+    return {m.group(1): int(m.group(2)) for m in re.finditer(rf"\b({prefix}[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+
+
+def test_binding_enums_match_header():
+    src = _header()
+    piv = _enum_values(src, "ACI_PIVOT_")
+    assert {k: piv["ACI_PIVOT_" + k.upper()] for k in binding.PIVOT_MODES} == binding.PIVOT_MODES
+    ovl = _enum_values(src, "ACI_OVERLAP_")
+    assert {k: ovl["ACI_OVERLAP_" + k.upper()] for k in binding.OVERLAP_MODES} == binding.OVERLAP_MODES
+    prec = _enum_values(src, "ACI_PREC_")
+    assert {k: prec["ACI_PREC_" + k.upper()] for k in binding.PRECISIONS} == binding.PRECISIONS
+
+
+def test_opts_fields_match_header_order():
+    src = _header()
+    body = re.search(r"typedef struct \{([^{}]*?)\} aci_opts;", src, flags=re.S).group(1)
+    fields = [m.group(1) for m in re.finditer(r"\b(?:int32_t|uint64_t|double)\s+(\w+)\s*;", body)]
+    fields += [m.group(1) for m in re.finditer(r"const aci_tt \*(\w+)\s*;", body)]
+    names = [f[0] for f in binding.AciOpts._fields_]
+    assert sorted(names) == sorted(fields), (names, fields)
+    # declaration order (pointers included) is the struct's memory order
+    order = [m.group(1) for m in re.finditer(r"(?:int32_t|uint64_t|double|const aci_tt \*)\s*(\w+)\s*;", body)]
+    assert names == order, (names, order)
