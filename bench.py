@@ -23,6 +23,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -355,7 +356,8 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        log_dir = os.environ.get("ACI_BENCH_LOG_DIR", tempfile.gettempdir())
+        self.path = os.path.join(log_dir, f"clocks_rank{index}.csv")
 
     def start(self):
         try:

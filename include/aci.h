@@ -70,7 +70,7 @@ typedef enum { ACI_TOL_REL = 0, ACI_TOL_ABS = 1 } aci_tol_kind;
  *                  position, bond, previous membership), keeps the ceil(keep * k_prev) + 8 best
  *                  of each, forms Pi on them only and runs the full search there. Right-to-left
  *                  sweeps stay the full search: they produce the output and the error estimates
- *                  of the stop test, so plain ACI remains the judge and the fallback. */
+ *                  of the stop test, so plain ACI remains the arbiter and the fallback. */
 typedef enum { ACI_PIVOT_FULL = 0, ACI_PIVOT_ROOK = 1, ACI_PIVOT_PROPOSED = 2 } aci_pivot_mode;
 /* Arithmetic of the contractions (the frame half-products of Algorithm 5 and the Pi blocks of
  * Eq. (pifromframes)). The pivot search (Algorithm 2), its Schur updates and error estimates and

@@ -1072,7 +1072,7 @@ struct Run {
             }
             for (int b = 0; b < nb; ++b) {  // left to right, CI "right"
                 left_half(b);
-                if (proposed) {  // the learned restriction; the full right-to-left sweep stays the judge
+                if (proposed) {  // the learned restriction; the full right-to-left sweep stays the arbiter
                     proposed_update(b);
                     continue;
                 }
