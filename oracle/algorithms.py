@@ -103,8 +103,17 @@ def pivot_key(v):
 
 # ---------------------------------------------------------------- Algorithm 2: LDU (prrLU)
 
-def ldu(M, tau: float, chimax: int):
+def ldu(M, tau: float, chimax: int, follow=None, slack: float = 0.0):
     """Algorithm 2: in-place LDU with full-search pivoting (readings R2-R4).
+
+    ``follow`` = (rows, cols): another implementation's pivots (original positions, in pivot
+    order) to take instead of this function's own argmax wherever they are an equally valid
+    choice (R4: when two candidates' magnitudes differ by less than the rounding of the Schur
+    entries, either is correct). A followed pivot must lie within ``slack`` (absolute magnitude)
+    of the largest remaining one, and the followed rank must stop where the stop test allows it
+    within ``slack`` of tau; each breach is appended to the result's ``violations`` (and this
+    function's own choice is taken there). ``differ`` counts the steps where a followed pivot
+    was not this function's own argmax.
 
     Returns a dict with
       L  (m x k) unit lower triangular in pivot order, rows in M's original row order,
@@ -121,9 +130,13 @@ def ldu(M, tau: float, chimax: int):
     chi = 0
     eps = 0.0
     best_list, second_list = [], []
+    violations, differ = [], 0
+    kfollow = len(follow[0]) if follow is not None else None
     while True:
         if chi == min(m, n):
             eps = 0.0
+            if follow is not None and kfollow != chi:
+                violations.append((chi, "followed rank differs at an exhausted block"))
             break
         sub = S[chi:, chi:]
         key = pivot_key(sub)
@@ -133,7 +146,31 @@ def ldu(M, tau: float, chimax: int):
         i, j = where[int(np.argmin(lin))] + chi
         piv = S[i, j]
         mag = float(magnitude(piv))
-        if chi == chimax or (chi >= 1 and mag <= tau):
+        stop = chi == chimax or (chi >= 1 and mag <= tau)
+        if follow is not None:
+            if chi >= kfollow:  # the other side stopped here: allowed if the stop test holds within slack
+                if not (stop or mag <= tau + slack):
+                    violations.append((chi, f"followed rank stops early: best {mag:.17g} > tau {tau:.17g}"))
+                eps = mag
+                break
+            # the other side accepted a pivot: allowed unless the stop test holds beyond slack
+            if chi == chimax or (chi >= 1 and mag < tau - slack):
+                violations.append((chi, "followed rank continues past the stop test"))
+            else:
+                pr = np.flatnonzero(I[chi:] == follow[0][chi])
+                pc = np.flatnonzero(J[chi:] == follow[1][chi])
+                if len(pr) != 1 or len(pc) != 1:
+                    violations.append((chi, "followed pivot is in a used row or column"))
+                else:
+                    fi, fj = pr[0] + chi, pc[0] + chi
+                    fmag = float(magnitude(S[fi, fj]))
+                    if fmag < mag - slack:
+                        violations.append((chi, f"followed pivot {fmag:.17g} below the maximum {mag:.17g}"))
+                    elif (fi, fj) != (i, j):
+                        differ += 1
+                        i, j, piv, mag = fi, fj, S[fi, fj], fmag
+            stop = False
+        if stop:
             eps = mag
             break
         flat = key.reshape(-1).copy()
@@ -168,7 +205,8 @@ def ldu(M, tau: float, chimax: int):
     L[I, :] = Lp  # undo the row permutation: L[I[pos]] = Lp[pos]
     U[:, J] = Up
     return dict(L=L, D=D, U=U, I=I[:k].copy(), J=J[:k].copy(), eps=eps, k=k,
-                best=np.array(best_list), second=np.array(second_list))
+                best=np.array(best_list), second=np.array(second_list), violations=violations,
+                differ=differ)
 
 
 def _argmax_free(key, free):
@@ -271,10 +309,12 @@ def ldu_rook(M, tau: float, chimax: int):
 PIVOT_MODES = ("full", "rook")
 
 
-def factorise(M, tau: float, chimax: int, pivot_mode: str = "full"):
+def factorise(M, tau: float, chimax: int, pivot_mode: str = "full", follow=None, slack: float = 0.0):
     """Algorithm 2 with the full search, or the rook search of reading R11."""
     if pivot_mode == "full":
-        return ldu(M, tau, chimax)
+        return ldu(M, tau, chimax, follow, slack)
+    if follow is not None:
+        raise ValueError("following another implementation's pivots is defined for the full search")
     if pivot_mode == "rook":
         return ldu_rook(M, tau, chimax)
     raise ValueError(pivot_mode)
@@ -289,9 +329,10 @@ def _inv_diag(D):
     return out
 
 
-def crossinterpolate(M, tau: float, chimax: int, leftorright: str = "right", pivot_mode: str = "full"):
+def crossinterpolate(M, tau: float, chimax: int, leftorright: str = "right", pivot_mode: str = "full",
+                     follow=None, slack: float = 0.0):
     """Algorithm 3: A, B with A @ B = L D U ~ M; "left" puts P^-1 into A, "right" into B."""
-    f = factorise(M, tau, chimax, pivot_mode)
+    f = factorise(M, tau, chimax, pivot_mode, follow, slack)
     L, D, U, I, J = f["L"], f["D"], f["U"], f["I"], f["J"]
     if leftorright == "left":
         LI = L[I, :]  # k x k unit lower
@@ -308,11 +349,12 @@ def crossinterpolate(M, tau: float, chimax: int, leftorright: str = "right", piv
 
 # ---------------------------------------------------------------- Algorithm 4: local update
 
-def localupdate(Pi, tau: float, chimax: int, leftorright: str, pivot_mode: str = "full"):
+def localupdate(Pi, tau: float, chimax: int, leftorright: str, pivot_mode: str = "full",
+                follow=None, slack: float = 0.0):
     """Algorithm 4: reshape Pi[alpha, s, s', beta] to M[(alpha, s), (s', beta)] and factorise."""
     a, d1, d2, b = Pi.shape
     M = Pi.reshape(a * d1, d2 * b)
-    f = crossinterpolate(M, tau, chimax, leftorright, pivot_mode)
+    f = crossinterpolate(M, tau, chimax, leftorright, pivot_mode, follow, slack)
     k = f["k"]
     f["Y"] = f["A"].reshape(a, d1, k)
     f["Y2"] = f["B"].reshape(k, d2, b)
@@ -393,14 +435,27 @@ def assemble_output(factors, L: int):
 
 def aci(inputs, op: str = "mul", tol: float = 1e-10, max_rank: int = 64, *,
         tol_kind: str = "rel", maxiter: int = 20, coef=None, init=None, seed: int = 0,
-        record: bool = False, pivot_mode: str = "full"):
+        record: bool = False, pivot_mode: str = "full", follow=None, follow_slack: float = 1e-12,
+        on_iteration=None):
     """Algorithm 1: alternating cross interpolation of f(X^1, ..., X^N).
 
     ``inputs`` is a list of N TTs (lists of cores (r, d, r')). Returns a dict with the
     output cores ``Y``, the ranks, the final pivot positions per bond (``I_pos``,
     ``J_pos``: row / column positions in that bond's Pi matrix, from the last sweep),
-    ``eps`` per bond (last iteration, both half-sweeps), ``iterations``, ``S`` and, if
-    ``record``, the per-pivot magnitudes needed to detect near-ties.
+    ``eps`` per bond (last iteration, both half-sweeps), ``iterations``, ``S``, the pivots
+    of every local update (``history``: {(u, b): (rows, cols)} with u = 0 for the initial
+    CI, whose update of site s is filed under bond s - 1, and u = 1 + 2 (i - 1) + h for
+    half-sweep h = 0 (left to right) / 1 (right to left) of iteration i) and, if ``record``,
+    the per-pivot magnitudes needed to detect near-ties.
+
+    ``follow``: a history in that format from another implementation. Every local update
+    then takes the other side's pivots wherever they are as valid as its own (see ldu: within
+    ``follow_slack`` times the scale of the matrix, S or max|M| for the initial CI), and the
+    result's ``follow`` entry counts the updates and pivots compared, the steps where the two
+    choices differed (near-ties) and lists every breach. Full search only.
+
+    ``on_iteration(i)``, if given, is called after iteration i (both half-sweeps and the stop
+    test) with no effect on the computation (used to time the oracle sweep by sweep).
     """
     N = len(inputs)
     L = len(inputs[0])
@@ -431,12 +486,31 @@ def aci(inputs, op: str = "mul", tol: float = 1e-10, max_rank: int = 64, *,
     Lf = [{-1: np.ones((1, 1), dtype=dt)} for _ in range(N)]
     Rf = [{L: np.ones((1, 1), dtype=dt)} for _ in range(N)]
 
+    history = {}
+    freport = dict(updates=0, pivots=0, differ=0, violations=[])
+
+    def followed(u, b, f):
+        history[(u, b)] = (np.asarray(f["I"]).copy(), np.asarray(f["J"]).copy())
+        if follow is not None:
+            freport["updates"] += 1
+            freport["pivots"] += f["k"]
+            freport["differ"] += f["differ"]
+            freport["violations"] += [(u, b) + v for v in f["violations"]]
+
+    def fol(u, b):
+        if follow is None:
+            return None
+        if (u, b) not in follow:
+            raise ValueError(f"the followed history has no update {(u, b)}")
+        return follow[(u, b)]
+
     # ---- CI-canonicalisation of the initial guess, right to left (R7)
     for s in range(L - 1, 0, -1):
         r = Y[s].shape[0]
         M = Y[s].reshape(r, -1)
         tau0 = tol * _maxabs(M) if rel else tol
-        f = crossinterpolate(M, tau0, chimax, "right", pivot_mode)
+        f = crossinterpolate(M, tau0, chimax, "right", pivot_mode, fol(0, s - 1), follow_slack * _maxabs(M))
+        followed(0, s - 1, f)
         nj = len(J[s + 1])
         J[s] = [(int(q) // nj,) + J[s + 1][int(q) % nj] for q in f["J"]]
         Y[s] = f["B"].reshape(f["k"], dims[s], nj)
@@ -461,7 +535,9 @@ def aci(inputs, op: str = "mul", tol: float = 1e-10, max_rank: int = 64, *,
         Pi = fvals(blocks).astype(dt)
         S = max(S, _maxabs(Pi))
         tau = tol * S if rel else tol
-        f = localupdate(Pi, tau, chimax, direction, pivot_mode)
+        u = 1 + 2 * (iterations - 1) + (0 if direction == "right" else 1)
+        f = localupdate(Pi, tau, chimax, direction, pivot_mode, fol(u, b), follow_slack * S)
+        followed(u, b, f)
         ni = len(I[b - 1])
         nj = len(J[b + 2])
         I[b] = [I[b - 1][int(q) // dims[b]] + (int(q) % dims[b],) for q in f["I"]]
@@ -493,6 +569,8 @@ def aci(inputs, op: str = "mul", tol: float = 1e-10, max_rank: int = 64, *,
         emax = max(max(eps_lr), max(eps_rl))
         grew = any(r > q for r, q in zip(ranks, ranks_prev))
         fixed = all(J[s] == J_prev[s] for s in range(1, L))
+        if on_iteration is not None:
+            on_iteration(it)
         if (not grew and emax <= tau) or fixed:
             break
         ranks_prev = ranks
@@ -503,7 +581,9 @@ def aci(inputs, op: str = "mul", tol: float = 1e-10, max_rank: int = 64, *,
                eps=[max(a, b) for a, b in zip(eps_lr, eps_rl)], eps_lr=list(eps_lr),
                eps_rl=list(eps_rl), I_pos=I_pos, J_pos=J_pos, S=S,
                I_sets={s: list(I[s]) for s in range(0, L - 1)},
-               J_sets={s: list(J[s]) for s in range(1, L)})
+               J_sets={s: list(J[s]) for s in range(1, L)}, history=history)
+    if follow is not None:
+        out["follow"] = freport
     if record:
         out["log"] = log
     return out

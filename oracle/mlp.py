@@ -1,5 +1,5 @@
 """CPU reference of the pivot-proposer network (TEST INFRASTRUCTURE ONLY, like the rest of
-``oracle``: imported by tests/ and bench.py's proposer leg, never by the library).
+``oracle``: imported by tests/ only, never by the library or the benchmark).
 
 Not in the paper: a small multilayer perceptron that scores candidate rows and columns of a Pi
 block (the learned proposer of the pivot search). Layout of the flat FP32 parameter vector, for

@@ -26,13 +26,19 @@ def tt_full(cores) -> np.ndarray:
 
 
 def tt_eval(cores, sigma: np.ndarray) -> np.ndarray:
-    """Values of a TT at multi-indices ``sigma`` (shape (P, L)), one product chain per point."""
+    """Values of a TT at multi-indices ``sigma`` (shape (P, L)), one product chain per point:
+    at each site the points are grouped by their local index, so each group is one matrix product."""
     sigma = np.asarray(sigma)
     P = sigma.shape[0]
     dtype = np.result_type(*[c.dtype for c in cores])
     v = np.ones((P, 1), dtype=dtype)
     for s, c in enumerate(cores):
-        v = np.einsum("pa,pab->pb", v, c[:, sigma[:, s], :].transpose(1, 0, 2))
+        out = np.empty((P, c.shape[2]), dtype=dtype)
+        for x in range(c.shape[1]):
+            m = sigma[:, s] == x
+            if m.any():
+                out[m] = v[m] @ c[:, x, :]
+        v = out
     return v[:, 0]
 
 
