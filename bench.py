@@ -33,10 +33,9 @@ if ROOT not in sys.path:
 
 METRIC = "ACI f(A,B) time vs χ at rel err ≤1e-8 (FP64 vs mixed/learned); % tensor peak"
 UNIT = "products/s"
-# FP64 vector peak of a GB300 (nominal 1.25 TFLOP/s: 152 SMs x ~2 DFMA/clk/SM at ~2.06 GHz);
-# a probe on this pool measured 1.197 TFLOP/s of DFMA throughput.
-FP64_PEAK_TFLOPS = 1.25
-SAMPLE_ITERS = 2
+# FP64 vector peak of a GB300, nominal 1.25 TFLOP/s (152 SMs x ~2 DFMA/clk/SM at ~2.06 GHz); the
+# rooflines use the library's own FP64 probe (aci_k_fp64_peak) measured in the same run instead.
+FP64_NOMINAL_TFLOPS = 1.25
 
 
 def parse():
@@ -48,12 +47,21 @@ def parse():
     ap.add_argument("--chi", type=int, default=128)
     ap.add_argument("--max-sweeps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-threads", type=int, default=1,
+                    help="reference arm: BLAS threads of the oracle (0: the library default); one thread is the "
+                         "faster on its matrices of at most a few hundred rows")
+    ap.add_argument("--no-time-to-tol", dest="time_to_tol", action="store_false",
+                    help="skip the per-sweep time and error curve")
+    ap.add_argument("--no-cfg3", dest="cfg3", action="store_false", help="skip the fused d = 8 sub-object")
+    ap.add_argument("--cfg3-chi", type=int, default=128)
+    ap.add_argument("--batch-line", type=int, default=64,
+                    help="pairs of the batched workload in the default line's batch object (0: skip it)")
     ap.add_argument("--mixed-digits", type=int, default=6, help="BF16 digit planes of the mixed run (0: skip it)")
     ap.add_argument("--precision", default="fp64", help="contractions of the headline run: fp64 or bf16xS")
     ap.add_argument("--pivot-mode", default="full", choices=["full", "rook"])
     ap.add_argument("--overlap", default="auto", choices=["auto", "off", "on"],
                     help="schedule of the sweeps (aci_opts.sweep_overlap)")
-    ap.add_argument("--kernel", default="", choices=["", "pi_block", "frame_gemm", "prrlu"],
+    ap.add_argument("--kernel", default="", choices=["", "pi_block", "frame_gemm", "prrlu", "fp64peak"],
                     help="time one step-level call of this shape instead of the product (kernel profiling)")
     ap.add_argument("--m", type=int, default=2048)
     ap.add_argument("--n", type=int, default=2048)
@@ -95,7 +103,7 @@ def run_proposer(args):
     gen_s = time.time() - t0
     print(f"proposer: {nsteps} steps generated in {gen_s:.1f} s", file=sys.stderr, flush=True)
     import torch
-    from oracle import mlp
+    from synthetic.weights import proposer_init
     from paper_2604_00037_gb300.binding import Context
     from synthetic.tt import tt_eval
     ctx = Context(0)
@@ -107,7 +115,7 @@ def run_proposer(args):
         ctx.elementwise(dev(a), dev(b), "mul", tol, max_rank, max_sweeps=args.max_sweeps)
     X, y, nrec = read()
     pos = float(y.mean().item())
-    P = torch.from_numpy(mlp.init(0, 7)).cuda()
+    P = torch.from_numpy(proposer_init(0, 7)).cuda()
     M, V = torch.zeros_like(P), torch.zeros_like(P)
     t1 = time.time()
     for it in range(1, 401):
@@ -174,55 +182,18 @@ def run_proposer(args):
     ctx.close()
 
 
-def _make_pair(spec):
-    from synthetic.fields import batch_config4_pair
-    return batch_config4_pair(spec)
-
-
 def run_batch(args):
-    """The batched workload: args.batch pairs of uneven length and rank (synthetic/fields.py,
-    batch_config4_spec), FP64, each product exactly as aci_elementwise_ex computes it. Times the
-    whole batch through aci_elementwise_batch with one product in flight and with args.streams
-    (library default when 0), after a warm-up batch; inputs are device-resident."""
-    import multiprocessing as mp
-    from synthetic.fields import batch_config4_spec
-    spec = batch_config4_spec(n=args.batch)
-    t0 = time.time()
-    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[v] = "1"  # one BLAS thread per generator process (inherited by the pool)
-    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:  # before any GPU call
-        pairs = pool.map(_make_pair, spec)
-    gen_s = time.time() - t0
+    """The batched workload alone: args.batch pairs (synthetic/fields.py, batch_config4_spec) through
+    aci_elementwise_batch, one product at a time and concurrently (autotuned), device-resident inputs."""
+    spec, pairs, gen_s = make_batch(args.batch)
     print(f"batch: {len(pairs)} pairs generated in {gen_s:.1f} s", file=sys.stderr, flush=True)
     import torch
     from paper_2604_00037_gb300.binding import Context
     ctx = Context(0)
-    items = [dict(a=[torch.from_numpy(c).cuda() for c in a], b=[torch.from_numpy(c).cuda() for c in b],
-                  op=sp["op"], tol=sp["tol"], max_rank=sp["max_rank"]) for sp, (a, b) in zip(spec, pairs)]
-    out = {}
-    for label, streams in (("sequential", 1), ("concurrent", args.streams)):
-        ctx.elementwise_batch(items[: min(4, len(items))], streams=streams, max_sweeps=args.max_sweeps)
-        torch.cuda.synchronize()
-        times = []
-        for _ in range(max(1, args.steps)):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            res = ctx.elementwise_batch(items, streams=streams, max_sweeps=args.max_sweeps)
-            e1.record()
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-            print(f"batch: {label} streams={streams} {times[-1]:.0f} ms", file=sys.stderr, flush=True)
-        ms = statistics.median(times)
-        out[label] = {"streams": streams, "ms_per_batch": ms, "products_per_s": len(items) / (ms / 1e3),
-                      "statuses": sorted({r[1]["status"] for r in res})}
-    line = {"metric": "batched ACI products/s (independent pairs of uneven L and chi)", "unit": "products/s",
-            "value": out["concurrent"]["products_per_s"], "higher_is_better": True, "dtype": "f64",
-            "data": "synthetic", "n_gpus": 1, "steps": args.steps,
-            "config": {"workload": f"{len(items)} pairs of 2D interleaved Fourier fields, L in [20, 40], "
-                                   f"chi in [16, 256], a*b / a*conj(b), tol 1e-8 rel, max_rank chi",
-                       "input_generation_s": gen_s},
-            "sequential": out["sequential"], "concurrent": out["concurrent"],
-            "speedup": out["sequential"]["ms_per_batch"] / out["concurrent"]["ms_per_batch"]}
+    line = run_batch_line(ctx, spec, pairs, gen_s, args, torch.cuda.current_stream(), reps=max(1, args.steps))
+    line = {"metric": "batched ACI products/s (independent pairs of uneven L and chi)", "higher_is_better": True,
+            "dtype": "f64 (odd pairs handed over in FP32)", "data": "synthetic", "n_gpus": 1, "steps": args.steps,
+            **line}
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -241,6 +212,13 @@ def run_kernel(args):
         if args.complex:
             x = x + 1j * rng.standard_normal((r, c))
         return torch.from_numpy(x).cuda()
+    if args.kernel == "fp64peak":
+        t = [ctx.fp64_peak() for _ in range(max(1, args.steps))]
+        print(json.dumps({"kernel": "fp64peak", "tflops": t, "median_tflops": statistics.median(t),
+                          "note": "aci_k_fp64_peak: 8 CTAs of 512 threads per SM, 8 independent FP64 FMA "
+                                  "chains per thread, CUDA events"}), flush=True)
+        ctx.close()
+        return
     if args.kernel == "pi_block":
         A, B = mat(args.m, args.k), mat(args.k, args.n)
         call = lambda: ctx.pi_block([A], [B], "abs2_mul", precision=args.precision)
@@ -300,17 +278,16 @@ def config_dict(args, p):
 
 # ------------------------------------------------------------------------------ CPU oracle
 
-def oracle_sample(p, max_sweeps):
-    """Time the oracle on the first SAMPLE_ITERS sweeps of the product; extrapolate to a product.
-
-    Returns (estimated seconds per product, sample seconds, threads)."""
+def oracle_product(p, max_sweeps, max_iters=None):
+    """One oracle product of the workload, timed sweep by sweep (wall clock). Returns (total seconds,
+    cumulative seconds after each sweep iteration, iterations run). ``max_iters`` stops it early."""
     import oracle
     a, b = p["inputs"]
+    marks = []
     t0 = time.perf_counter()
-    oracle.aci([a, b], "mul", p["tol"], p["max_rank"], maxiter=SAMPLE_ITERS)
-    t = time.perf_counter() - t0
-    per_product = t * max_sweeps / SAMPLE_ITERS
-    return per_product, t
+    oracle.aci([a, b], "mul", p["tol"], p["max_rank"], maxiter=max_iters or max_sweeps,
+               on_iteration=lambda it: marks.append(time.perf_counter() - t0))
+    return time.perf_counter() - t0, marks, len(marks)
 
 
 def blas_threads():
@@ -319,26 +296,77 @@ def blas_threads():
         n = [i.get("num_threads", 1) for i in threadpool_info()]
         return max(n) if n else 1
     except Exception:
-        return os.cpu_count() or 1
+        env = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS")
+        return int(env) if env else (os.cpu_count() or 1)
+
+
+def oracle_subprocess(chi, max_sweeps, threads, iters=None):
+    """One oracle product in a child process with `threads` BLAS threads (the count is fixed when
+    numpy loads). Returns (seconds, sweeps) or None."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=str(threads), OMP_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "p = bench.workload(%d); t, m, n = bench.oracle_product(p, %d, %s); print(json.dumps([t, n]))"
+            % (ROOT, chi, max_sweeps, repr(iters)))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+        t, n = json.loads(r.stdout.strip().splitlines()[-1])
+        return t, n
+    except Exception:
+        return None
+
+
+def cpu_baseline_line(p, args):
+    """The oracle timed on this host, one whole product each way: with every BLAS thread (in this
+    process) and with one thread (a child process; the paper times one CPU thread). The value is
+    the faster of the two (its matrices are at most a few hundred wide, where one thread can win)."""
+    total, marks, iters = oracle_product(p, args.max_sweeps)
+    allc = {"value": 1.0 / total, "cores": blas_threads(), "seconds_per_product": total, "sweeps": iters}
+    one = oracle_subprocess(args.chi, args.max_sweeps, 1)
+    out = {"unit": UNIT, "kind": "oracle", "all_threads": allc}
+    best = allc
+    if one:
+        out["one_thread"] = {"value": 1.0 / one[0], "cores": 1, "seconds_per_product": one[0], "sweeps": one[1]}
+        if out["one_thread"]["value"] > best["value"]:
+            best = out["one_thread"]
+    out.update(value=best["value"], cores=best["cores"],
+               sample=f"one whole product of the workload (initial CI and all {best['sweeps']} sweeps actually run) "
+                      f"with {best['cores']} BLAS thread(s): {best['seconds_per_product']:.1f} s wall clock; the "
+                      f"other thread count is reported beside it")
+    return out
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, sweep by sweep. A step is one sweep iteration of the
+    workload's product (the first step of a product also carries its initial CI); K timed steps run
+    products back to back, each for up to max_sweeps iterations, so K = max_sweeps is one whole
+    product. value = products completed per second = (steps / sweeps per product) / seconds."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.oracle_threads > 0:  # before numpy loads: its BLAS fixes the thread count then
+        for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = str(args.oracle_threads)
     p = workload(args.chi)
-    for _ in range(args.warmup):
-        oracle_sample(p, args.max_sweeps)
-    est = []
-    for _ in range(args.steps):
-        per, t = oracle_sample(p, args.max_sweeps)
-        est.append(per)
-    value = len(est) / sum(est)
+    if args.warmup:
+        oracle_product(p, args.max_sweeps, max_iters=min(args.warmup, args.max_sweeps))
+    done, total, products, per = 0, 0.0, 0, None
+    while done < args.steps:
+        n = min(args.max_sweeps, args.steps - done)
+        t, marks, iters = oracle_product(p, args.max_sweeps, max_iters=n)
+        if per is None:
+            per = iters if n == args.max_sweeps else args.max_sweeps
+        total += t
+        done += iters
+        products += 1
+        if iters < n:  # the product converged early: its remaining steps do not exist
+            break
+    value = (done / per) / total
     cores = blas_threads()
-    sample = (f"each step: the CPU oracle's initial CI and first {SAMPLE_ITERS} of {args.max_sweeps} sweeps of "
-              f"the same product; per-product time = sample time x {args.max_sweeps}/{SAMPLE_ITERS}")
+    sample = (f"each step = one sweep iteration of the oracle's product (the first of each product also runs "
+              f"its initial CI); {done} steps timed as {products} product run(s), {per} sweeps per product")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(done, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(args, p),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
@@ -419,11 +447,198 @@ def recorded_traffic(kernel_class):
     return None
 
 
-def mean_pi_bytes(ranks, d=2):
-    """Mean bytes of one Π block (FP64) over the bonds at the final ranks: the input block a
-    pivot-search launch reads."""
-    nb = len(ranks) - 2
-    return sum(8.0 * d * ranks[b] * d * ranks[b + 2] for b in range(nb)) / max(nb, 1)
+def update_order(L, iterations):
+    """Local updates of a product in execution order, as pivot-history keys (u, bond)."""
+    order = [(0, s - 1) for s in range(L - 1, 0, -1)]
+    for it in range(1, iterations + 1):
+        order += [(1 + 2 * (it - 1), b) for b in range(L - 1)]
+        order += [(2 + 2 * (it - 1), b) for b in range(L - 2, -1, -1)]
+    return order
+
+
+def pivot_work(info, d, max_rank, in_ranks, elem_bytes=8):
+    """From one product's pivot history: pivot-search launches, accepted pivots, pivot steps (each
+    launch also takes one step that ends in the stop decision unless its block is used up) and the
+    algorithmic bytes of the blocks the launches factorise (each read once)."""
+    import numpy as np
+    hist = info["history"]
+    L = len(d)
+    cap = [1] + [min(max_rank, 2 ** min(s, 62), int(np.prod(d[:s], dtype=float)), int(np.prod(d[s:], dtype=float)))
+                 for s in range(1, L)] + [1]
+    ranks = [1] * (L + 1)
+    launches = pivots = steps = 0
+    nbytes = 0.0
+    for (u, b) in update_order(L, info["iterations"]):
+        k = len(hist[(u, b)][0])
+        if u == 0:  # initial CI of site s = b + 1: (initial-guess rank) x (d_s rank_{s+1})
+            s_ = b + 1
+            m, n = min(cap[s_], *[r[s_] for r in in_ranks]), d[s_] * ranks[s_ + 1]
+        else:
+            m, n = ranks[b] * d[b], d[b + 1] * ranks[b + 2]
+        ranks[b + 1] = k
+        launches += 1
+        pivots += k
+        steps += k + (0 if k == min(m, n) else 1)
+        nbytes += float(m) * n * elem_bytes
+    return dict(launches=launches, pivots=pivots, steps=steps, block_bytes=nbytes)
+
+
+def sample_points(rng, L, d, n):
+    import numpy as np
+    return rng.integers(0, d, size=(n, L))
+
+
+def rel_err(y, ref):
+    import numpy as np
+    return float(np.abs(y - ref).max() / np.abs(ref).max())
+
+
+def run_time_to_tol(ctx, A, B, a, b, p, args, stream):
+    """Device time and sampled error after each sweep: the call with max_sweeps = t, t = 1, 2, ..."""
+    import numpy as np
+    import torch
+    from synthetic.tt import tt_eval
+    pts = sample_points(np.random.default_rng(11), len(a), 2, 4000)
+    exact = tt_eval(a, pts) * tt_eval(b, pts)
+    rows = []
+    for t in range(1, args.max_sweeps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        y, info = ctx.elementwise(A, B, "mul", p["tol"], p["max_rank"], max_sweeps=t, overlap=args.overlap,
+                                  precision=args.precision, pivot_mode=args.pivot_mode)
+        e1.record(stream)
+        e1.synchronize()
+        err = rel_err(tt_eval([c.cpu().numpy() for c in y], pts), exact)
+        rows.append({"sweeps": info["iterations"], "ms": e0.elapsed_time(e1), "rel_err_vs_exact": err,
+                     "max_eps_rel": info["max_eps"] / info["scale"], "max_rank": max(info["ranks"])})
+        if info["iterations"] < t:
+            break
+    first = next((r for r in rows if r["rel_err_vs_exact"] <= 1e-8), None)
+    return {"target_rel_err": 1e-8, "points": len(pts), "per_sweep": rows,
+            "first_sweep_at_target": first["sweeps"] if first else None,
+            "ms_at_target": first["ms"] if first else None,
+            "note": "a row per max_sweeps = t call (device time of the whole call, CUDA events); the error is "
+                    "the max relative error against the exact product on seeded grid points"}
+
+
+def run_cfg3(ctx, args, stream, fp64_peak):
+    """The fused d = 8 workload: |psi|^2 psi of a 3D complex field, 12 sites, chi = 128, tol 1e-8,
+    max_rank chi, in FP64 and with BF16 digit-plane contractions (plain schedule at d = 8)."""
+    import numpy as np
+    import torch
+    from synthetic import config_inputs
+    from synthetic.tt import tt_eval
+    p = config_inputs(3, args.cfg3_chi)
+    a = p["inputs"][0]
+    A = [torch.from_numpy(c).cuda() for c in a]
+    pts = sample_points(np.random.default_rng(12), len(a), 8, 4000)
+    psi = tt_eval(a, pts)
+    exact = (psi.real ** 2 + psi.imag ** 2) * psi
+    out = {"workload": f"3D quantics, 12 sites of d = 8 (2^36 points), complex128 500-mode field, chi = "
+                       f"{args.cfg3_chi}, |psi|^2 psi, tol {p['tol']:g} rel, max_rank {p['max_rank']}"}
+    vals = {}
+    prec_list = ["fp64"] + ([f"bf16x{args.mixed_digits}"] if args.mixed_digits else [])
+    for prec in prec_list:
+        call = lambda prof: ctx.elementwise(A, None, "abs2_mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps,
+                                            precision=prec, profile=prof)
+        call(False)
+        ts = []
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            y, info = call(False)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        _, pinfo = call(True)
+        yv = tt_eval([c.cpu().numpy() for c in y], pts)
+        vals[prec] = yv
+        k = pinfo["kernels"]
+        ent = {"ms_per_product": statistics.median(ts), "iterations": info["iterations"],
+               "max_rank": max(info["ranks"]), "rel_err_vs_exact": rel_err(yv, exact),
+               "classes_ms": {c: k[c]["ms"] for c in k}}
+        if prec == "fp64":
+            cms = k["frame"]["ms"] + k["pi"]["ms"]
+            cfl = k["frame"]["flops"] + k["pi"]["flops"]
+            ach = cfl / (cms / 1e3) / 1e12
+            ent["roofline_fp64"] = {"bound": "alu", "kernel": "gemm_kernel (frames and Pi)", "achieved": ach,
+                                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                                    "peak_source": "FP64 FMA probe (aci_k_fp64_peak), measured in this run"}
+        else:
+            tms = k["frame"]["ms"] + k["pi"]["ms"]
+            tfl = k["frame"]["tensor_flops"] + k["pi"]["tensor_flops"]
+            peak, src = measured_peak("bf16_tflops", 1900.0)
+            ach = tfl / (tms / 1e3) / 1e12
+            ent["rel_err_vs_fp64"] = rel_err(yv, vals["fp64"])
+            ent["roofline_tensor"] = {"bound": "tensor", "kernel": "tc_split_kernel + tc_gemm_kernel (frames and Pi)",
+                                      "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                                      "peak_source": f"bf16 dense, {src} (burst)",
+                                      "note": "BF16 MMA flops issued / device time of the contraction launches"}
+        out[prec] = ent
+    if len(prec_list) > 1:
+        out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_product"] / out[prec_list[1]]["ms_per_product"]
+    return out
+
+
+def _batch_pair(spec):
+    from synthetic.fields import batch_config4_pair
+    return batch_config4_pair(spec)
+
+
+def make_batch(n):
+    """The batched workload's inputs, generated in a spawned pool (before any GPU call)."""
+    import multiprocessing as mp
+    from synthetic.fields import batch_config4_spec
+    spec = batch_config4_spec(n=n)
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"  # one BLAS thread per generator process (inherited by the pool)
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        pairs = pool.map(_batch_pair, spec)
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.pop(v, None)
+    return spec, pairs, time.time() - t0
+
+
+def batch_items(spec, pairs):
+    import torch
+    items = []
+    for sp, (a, b) in zip(spec, pairs):
+        dt = torch.float32 if sp["dtype"] == "f32" else torch.float64
+        items.append(dict(a=[torch.from_numpy(c).to(dt).cuda() for c in a],
+                          b=[torch.from_numpy(c).to(dt).cuda() for c in b],
+                          op=sp["op"], tol=sp["tol"], max_rank=sp["max_rank"]))
+    return items
+
+
+def run_batch_line(ctx, spec, pairs, gen_s, args, stream, reps=1, streams_list=(1, 0)):
+    import numpy as np
+    import torch
+    items = batch_items(spec, pairs)
+    ctx.elementwise_batch(items[: min(4, len(items))], streams=1, max_sweeps=args.max_sweeps)
+    out = {}
+    for streams in streams_list:
+        label = "one_at_a_time" if streams == 1 else "concurrent"
+        if streams == 0:  # the autotuner's trial calls come first, untimed
+            for _ in range(3):
+                ctx.elementwise_batch(items, streams=0, max_sweeps=args.max_sweeps)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = ctx.elementwise_batch(items, streams=streams, max_sweeps=args.max_sweeps)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        out[label] = {"streams": streams if streams else "autotuned", "ms_per_batch": ms,
+                      "products_per_s": len(items) / (ms / 1e3),
+                      "statuses": sorted({r[1]["status"] for r in res})}
+    return {"workload": f"{len(items)} pairs of 2D interleaved 200-mode Fourier fields, L in [20, 40], chi in "
+                        f"[16, 256], even pairs FP64 and odd pairs FP32, a*b / a*conj(b), tol 1e-8 rel, max_rank chi",
+            "value": out["concurrent"]["products_per_s"], "unit": "products/s",
+            **out, "speedup": out["one_at_a_time"]["ms_per_batch"] / out["concurrent"]["ms_per_batch"],
+            "input_generation_s": gen_s}
 
 
 def main():
@@ -437,12 +652,15 @@ def main():
     if args.proposer:
         return run_proposer(args)
     import numpy as np
-    import torch
-    import torch.distributed as dist
-
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    batch = None
+    if args.batch_line and rank == 0 and world == 1:
+        batch = make_batch(args.batch_line)  # spawned pool: before any GPU call
+    import torch
+    import torch.distributed as dist
+
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -455,14 +673,16 @@ def main():
     ctx = Context(local)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    fp64_peak = ctx.fp64_peak()
 
-    def step(profile):
+    def step(profile=False, history=False):
         return ctx.elementwise(A, B, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps, profile=profile,
-                               precision=args.precision, pivot_mode=args.pivot_mode, overlap=args.overlap)
+                               precision=args.precision, pivot_mode=args.pivot_mode, overlap=args.overlap,
+                               history=history)
 
     for w in range(args.warmup):
         flush.fill_(w & 0xFF)
-        step(False)
+        step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -475,7 +695,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        y, info = step(True)
+        y, info = step()
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -492,44 +712,55 @@ def main():
         total_ms = float(t.item())
     value = world * args.steps / (total_ms / 1e3)
 
-    # per-kernel-class roofline from the library's CUDA events of the timed steps
+    # One more product with per-launch CUDA events (the library times every kernel on its stream)
+    # and the pivot history: the class breakdown and the pivot search's roofline and latency.
+    flush.fill_(3)
+    _, dinfo = step(profile=True, history=True)
     classes = ("frame", "pi", "pivot", "other")
-    kms = {c: sum(i["kernels"][c]["ms"] for i in infos) for c in classes}
-    kcnt = {c: sum(i["kernels"][c]["count"] for i in infos) for c in classes}
-    kfl = {c: sum(i["kernels"][c]["flops"] for i in infos) for c in classes}
+    kms = {c: dinfo["kernels"][c]["ms"] for c in classes}
+    kcnt = {c: dinfo["kernels"][c]["count"] for c in classes}
+    kfl = {c: dinfo["kernels"][c]["flops"] for c in classes}
+    work = pivot_work(dinfo, [2] * len(a), p["max_rank"], [[1] + [c.shape[2] for c in x] for x in (a, b)])
     dom = max(("frame", "pi", "pivot"), key=lambda c: kms[c])
     achieved = kfl[dom] / (kms[dom] / 1e3) / 1e12
     ratio = recorded_traffic(dom)
-    traffic = ratio * mean_pi_bytes(infos[-1]["ranks"]) if ratio is not None and dom == "pivot" else None
+    traffic = ratio * work["block_bytes"] / work["launches"] if ratio is not None and dom == "pivot" else None
+    wall = dinfo["device_ms"]
     roofline = {"bound": "alu", "kernel": {"frame": "gemm_kernel (frame half-products)",
                                            "pi": "gemm_kernel (Pi block + f)",
-                                           "pivot": "prrlu_kernel"}[dom],
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
+                                           "pivot": "prrlu_creg_kernel / prrlu_cluster_kernel / prrlu_kernel"}[dom],
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                 "traffic": traffic,
                 "traffic_note": ("DRAM bytes per launch: the ncu ratio of DRAM bytes to input-block bytes "
-                                 "(profiles/prrlu_creg_kernel_480x480_k240.md) times the mean Π block at the "
-                                 "final ranks" if traffic is not None else "no capture of the current kernel source"),
-                "peak_source": "FP64 vector peak, nominal 1.25 TFLOP/s (no FP64 tensor path on GB300)",
-                "share": kms[dom] / total_ms * (world if world > 1 else 1),
-                "classes_ms_per_step": {c: kms[c] / args.steps for c in classes},
-                "classes_flops_per_step": {c: kfl[c] / args.steps for c in classes},
-                "classes_launches_per_step": {c: kcnt[c] / args.steps for c in classes}}
+                                 "(profiles/traffic.txt) times the mean block of this product's launches"
+                                 if traffic is not None else "no ncu capture of the current kernel source"),
+                "peak_source": f"FP64 FMA probe (aci_k_fp64_peak) measured in this run (nominal "
+                               f"{FP64_NOMINAL_TFLOPS} TFLOP/s; no FP64 tensor path on GB300)",
+                "share": kms[dom] / wall,
+                "profiled_product_ms": wall,
+                "classes_ms_per_step": kms, "classes_flops_per_step": kfl, "classes_launches_per_step": kcnt}
+    if dom == "pivot":
+        roofline["latency"] = {
+            "launches": work["launches"], "pivots": work["pivots"], "pivot_steps": work["steps"],
+            "us_per_pivot_step": kms["pivot"] * 1e3 / work["steps"],
+            "block_bytes": work["block_bytes"],
+            "l2_gbs": work["block_bytes"] / (kms["pivot"] / 1e3) / 1e9,
+            "note": "each pivot step is one argmax exchange of the sequential search; the blocks (<= 2 MB each) "
+                    "are read once per launch, from L2 or HBM: l2_gbs = block bytes / pivot-class time"}
 
     # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
     ah = [torch.from_numpy(c).pin_memory().numpy() for c in a]
     bh = [torch.from_numpy(c).pin_memory().numpy() for c in b]
     h2d = sum(c.nbytes for c in ah) + sum(c.nbytes for c in bh)
-    ctx.elementwise(ah, bh, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps, out_memory="host",
-                    precision=args.precision, pivot_mode=args.pivot_mode, overlap=args.overlap)
+    ekw = dict(max_sweeps=args.max_sweeps, out_memory="host", precision=args.precision, pivot_mode=args.pivot_mode,
+               overlap=args.overlap)
+    ctx.elementwise(ah, bh, "mul", p["tol"], p["max_rank"], **ekw)
     e2e_t, d2h = [], 0
     for k in range(max(1, min(args.steps, 3))):
         flush.fill_(k & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        yh, _ = ctx.elementwise(ah, bh, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps,
-                                out_memory="host", precision=args.precision, pivot_mode=args.pivot_mode,
-                                overlap=args.overlap)
+        yh, _ = ctx.elementwise(ah, bh, "mul", p["tol"], p["max_rank"], **ekw)
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
         d2h = sum(c.nbytes for c in yh)
@@ -539,13 +770,14 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_value = world * len(e2e_t) / float(t.item())
 
+    ttt = run_time_to_tol(ctx, A, B, a, b, p, args, stream) if args.time_to_tol and rank == 0 else None
+
     # the same workload with the contractions on the tensor cores; errors on 20000 sampled points
     mixed = None
     if args.mixed_digits:
         from synthetic.tt import tt_eval
         prec = f"bf16x{args.mixed_digits}"
-        rng = np.random.default_rng(8)
-        pts = rng.integers(0, 2, size=(20000, len(a)))
+        pts = sample_points(np.random.default_rng(8), len(a), 2, 20000)
         exact = tt_eval(a, pts) * tt_eval(b, pts)
         y64 = tt_eval([c.cpu().numpy() for c in y], pts)
 
@@ -553,40 +785,39 @@ def main():
             return ctx.elementwise(A, B, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps, profile=profile,
                                    precision=prec, overlap=args.overlap)
         mstep(False)
-        mt, minfo = [], []
+        mt = []
         for k in range(args.steps):
             flush.fill_((k + 3) & 0xFF)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ym, info = mstep(True)
+            ym, _ = mstep(False)
             e1.record(stream)
             e1.synchronize()
             mt.append(e0.elapsed_time(e1))
-            minfo.append(info)
+        _, minfo = mstep(True)
         yv = tt_eval([c.cpu().numpy() for c in ym], pts)
-        scale = np.abs(exact).max()
-        tms = sum(i["kernels"][c]["ms"] for i in minfo for c in ("frame", "pi"))
-        tfl = sum(i["kernels"][c]["tensor_flops"] for i in minfo for c in ("frame", "pi"))
+        k_ = minfo["kernels"]
+        tms = k_["frame"]["ms"] + k_["pi"]["ms"]
+        tfl = k_["frame"]["tensor_flops"] + k_["pi"]["tensor_flops"]
         peak, src = measured_peak("bf16_tflops", 1900.0)
         ach = tfl / (tms / 1e3) / 1e12
         mixed = {"precision": prec, "value": world * args.steps / (sum(mt) / 1e3), "unit": UNIT,
                  "ms_per_step": sum(mt) / args.steps,
-                 "rel_err_vs_exact": float(np.abs(yv - exact).max() / scale),
-                 "rel_err_vs_fp64": float(np.abs(yv - y64).max() / scale),
-                 "fp64_rel_err_vs_exact": float(np.abs(y64 - exact).max() / scale),
-                 "classes_ms_per_step": {c: sum(i["kernels"][c]["ms"] for i in minfo) / args.steps for c in classes},
+                 "rel_err_vs_exact": rel_err(yv, exact), "rel_err_vs_fp64": float(np.abs(yv - y64).max() / np.abs(exact).max()),
+                 "fp64_rel_err_vs_exact": rel_err(y64, exact),
+                 "classes_ms_per_step": {c: k_[c]["ms"] for c in classes},
                  "roofline_tensor": {"bound": "tensor", "kernel": "tc_split_kernel + tc_gemm_kernel (frames and Pi)",
                                      "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                                      "peak_source": f"bf16 dense, {src} (burst)",
                                      "note": "BF16 MMA flops issued / device time of the contraction launches"}}
 
+    cfg3 = run_cfg3(ctx, args, stream, fp64_peak) if args.cfg3 and rank == 0 else None
+    batch_line = run_batch_line(ctx, *batch, args, stream) if batch is not None else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        per, t = oracle_sample(p, args.max_sweeps)
-        cpu = {"value": 1.0 / per, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-               "sample": f"the CPU oracle's initial CI and first {SAMPLE_ITERS} of {args.max_sweeps} sweeps of one "
-                         f"product ({t:.1f} s); per-product time = sample x {args.max_sweeps}/{SAMPLE_ITERS}"}
+        cpu = cpu_baseline_line(p, args)
 
     last = infos[-1]
     if rank == 0:
@@ -597,7 +828,8 @@ def main():
                 "data": "synthetic", "config": config_dict(args, p),
                 "result": {"iterations": last["iterations"], "converged": last["converged"],
                            "max_rank": max(last["ranks"]), "max_eps_rel": last["max_eps"] / last["scale"]},
-                "roofline": roofline, "cpu_baseline": cpu, "mixed": mixed,
+                "roofline": roofline, "fp64_peak_tflops": fp64_peak, "cpu_baseline": cpu,
+                "time_to_tol": ttt, "mixed": mixed, "cfg3": cfg3, "batch": batch_line,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
                 "clocks": clk}

@@ -41,7 +41,11 @@ typedef enum {
     ACI_E_NUMERIC = -7       /* a non-finite value reached a pivot                         */
 } aci_status;
 
-typedef enum { ACI_R64 = 0, ACI_C128 = 1 } aci_dtype;           /* FP64 real, complex128 */
+/* Element types of the input cores (a and b have the same dtype). The method runs in FP64 /
+ * complex128: FP32 and complex64 inputs are widened to FP64 / complex128 on load (exactly, in the
+ * library's kernels), and their outputs are FP64 / complex128. A warm-start TT may be FP32 or FP64
+ * of the inputs' kind (real or complex). */
+typedef enum { ACI_R64 = 0, ACI_C128 = 1, ACI_R32 = 2, ACI_C64 = 3 } aci_dtype;
 typedef enum { ACI_MEM_DEVICE = 0, ACI_MEM_HOST = 1 } aci_memory;
 
 /* Elementwise functions f (Sec. 2.1). N = 2 except ABS2_MUL (N = 1, b ignored).
@@ -169,6 +173,18 @@ typedef struct {
     double kernel_flops[4];    /* profile = 1: algorithmic flops per class                      */
     double tensor_flops[4];    /* profile = 1: BF16 tensor-core flops issued per class (digit-plane
                                   precisions; 0 for ACI_PREC_FP64)                               */
+    /* Pivot history (optional: all three NULL = not recorded; recording adds one small launch per
+     * local update). Local updates are numbered u = 0 for the CI-canonicalisation of the initial
+     * guess (its update of site s is stored at bond s - 1), then u = 1 + 2 (i - 1) + h for sweep
+     * iteration i = 1..max_sweeps, h = 0 left to right, h = 1 right to left. With
+     * U = 1 + 2 max_sweeps and B = L - 1:
+     *  hist_rank  [U * B]             rank of update u at bond b, at u * B + b (-1: did not run)
+     *  hist_rows  [U * B * max_rank]  its pivot rows (positions in the factorised matrix) in pivot
+     *                                 order, at (u * B + b) * max_rank + q
+     *  hist_cols  [U * B * max_rank]  its pivot columns, likewise                            */
+    int32_t *hist_rank;
+    int32_t *hist_rows;
+    int32_t *hist_cols;
 } aci_stats;
 
 /* Device memory hooks. alloc returns a device pointer of at least `bytes` bytes aligned to

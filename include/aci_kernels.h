@@ -115,6 +115,23 @@ aci_status aci_k_apply_pinv(aci_ctx *ctx, int32_t dtype, const void *T, int32_t 
  * x and y are device arrays of n doubles. */
 aci_status aci_k_reciprocal(aci_ctx *ctx, const double *x, int32_t n, double *y);
 
+/* Limits of the library's device-side waits for the context's later calls (no counterpart in the
+ * paper: a diagnostic of its failure detection). Every wait of a kernel on another CTA or on the
+ * tensor-core pipeline is bounded; when the bound is reached the kernel records a timeout, leaves
+ * its copies in flight to finish (their own wait keeps the default bound), returns, and the call
+ * returns ACI_E_TIMEOUT with its outputs untouched. exchange_polls > 0 bounds the pivot search's
+ * inter-CTA exchange waits (cooperative grid variant) to that many polls; pipeline_polls > 0 bounds
+ * the tensor-core contraction's copy and multiply waits likewise; 0 restores the default (2^24 polls,
+ * 2 s). Small values make an ordinary call run its waits out. Negative values give ACI_E_ARG. */
+aci_status aci_set_wait_limits(aci_ctx *ctx, int64_t exchange_polls, int64_t pipeline_polls);
+
+/* Throughput of the FP64 pipe (no counterpart in the paper: the denominator of the FP64
+ * rooflines the library's measurements quote). Runs `blocks` CTAs of 512 threads, each thread
+ * `iters` rounds of 8 independent FP64 fused multiply-adds, twice, and times the second run with
+ * CUDA events on the context stream. *tflops (host) = 2 x multiply-adds / seconds / 1e12.
+ * blocks in [1, 65535], iters in [1, 2^24], else ACI_E_ARG. */
+aci_status aci_k_fp64_peak(aci_ctx *ctx, int32_t blocks, int32_t iters, double *tflops);
+
 /* The pivot search of aci_k_prrlu for callers that cannot allocate device memory; the paper
  * has no counterpart (it concerns how this library obtains scratch memory, not the method).
  * Such callers include code inside a host application that owns all device memory and forbids
@@ -124,7 +141,10 @@ aci_status aci_k_reciprocal(aci_ctx *ctx, const double *x, int32_t n, double *y)
  * scratch is one 8 MiB file-scope device array that every GPU loading the library holds until
  * the process exits. Arguments and results are those of aci_k_prrlu, except:
  *  cuda_stream  the cudaStream_t to run on (NULL = legacy default stream), on the current device;
- *  limits       m <= 4096, n <= 4096, m * n <= 262144, else ACI_E_SHAPE and nothing runs.
+ *  limits       m <= 4096, n <= 4096, m * n <= 262144, else ACI_E_SHAPE and nothing runs. Every
+ *               shape within them runs: when the block takes the cooperative grid variant (m n >
+ *               2^18 real, > 2^16 complex), its grid is capped to what the array holds, so such a
+ *               call may use fewer CTAs than aci_k_prrlu (the results do not depend on it).
  * No aci_ctx is involved, so there is no aci_last_error() message: the status says what failed.
  * The first call on each device (with that device current) looks up the array's address; make
  * that first call before any stream capture. All calls on a device share the array: calls that

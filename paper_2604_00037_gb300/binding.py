@@ -18,7 +18,7 @@ from . import buildlib as _build
 # ---------------------------------------------------------------- C structures (mirror aci.h)
 
 ACI_OK, ACI_W_NOT_CONVERGED = 0, 1
-ACI_R64, ACI_C128 = 0, 1
+ACI_R64, ACI_C128, ACI_R32, ACI_C64 = 0, 1, 2, 3
 ACI_MEM_DEVICE, ACI_MEM_HOST = 0, 1
 OPS = {"mul": 0, "mul_conj": 1, "abs2_mul": 2, "affine": 3}
 TOL_KINDS = {"rel": 0, "abs": 1}
@@ -49,7 +49,8 @@ class AciStats(C.Structure):
                 ("ranks", C.POINTER(C.c_int64)), ("eps", C.POINTER(C.c_double)),
                 ("pivot_rows", C.POINTER(C.c_int32)), ("pivot_cols", C.POINTER(C.c_int32)),
                 ("kernel_ms", C.c_double * 4), ("kernel_count", C.c_int64 * 4), ("kernel_flops", C.c_double * 4),
-                ("tensor_flops", C.c_double * 4)]
+                ("tensor_flops", C.c_double * 4), ("hist_rank", C.POINTER(C.c_int32)),
+                ("hist_rows", C.POINTER(C.c_int32)), ("hist_cols", C.POINTER(C.c_int32))]
 
 KERNEL_CLASSES = ("frame", "pi", "pivot", "other")
 
@@ -78,7 +79,7 @@ EXPORTS = ["aci_create", "aci_destroy", "aci_last_error", "aci_opts_default", "a
            "aci_k_frame_gemm_prec", "aci_k_pi_block_prec", "aci_k_prrlu", "aci_k_prrlu_rook",
            "aci_k_tt_random", "aci_k_apply_pinv", "aci_k_prrlu_static", "aci_k_reciprocal",
            "aci_k_mlp_param_count", "aci_k_mlp_forward", "aci_k_mlp_grad", "aci_k_mlp_adam",
-           "aci_set_proposer", "aci_set_proposer_record"]
+           "aci_set_proposer", "aci_set_proposer_record", "aci_k_fp64_peak", "aci_set_wait_limits"]
 
 _lib = None
 
@@ -126,6 +127,8 @@ def load_library(build_if_missing: bool = True) -> C.CDLL:
     lib.aci_k_reciprocal.argtypes = [vp, vp, i32, vp]
     lib.aci_k_prrlu_static.argtypes = [vp, i32, vp, i32, i32, dbl, i32, vp, vp, vp, vp, vp,
                                        C.POINTER(i32), C.POINTER(dbl)]
+    lib.aci_k_fp64_peak.argtypes = [vp, i32, i32, C.POINTER(dbl)]
+    lib.aci_set_wait_limits.argtypes = [vp, i64, i64]
     lib.aci_k_mlp_param_count.argtypes = [i32]
     lib.aci_set_proposer.argtypes = [vp, vp, i32, C.c_float]
     lib.aci_set_proposer_record.argtypes = [vp, vp, i64, vp]
@@ -159,16 +162,14 @@ def make_op(op: str, coef=None) -> AciOp:
 def _dtype_code(x) -> int:
     import torch
     if isinstance(x, torch.Tensor):
-        if x.dtype == torch.float64:
-            return ACI_R64
-        if x.dtype == torch.complex128:
-            return ACI_C128
+        codes = {torch.float64: ACI_R64, torch.complex128: ACI_C128, torch.float32: ACI_R32,
+                 torch.complex64: ACI_C64}
     else:
-        if x.dtype == np.float64:
-            return ACI_R64
-        if x.dtype == np.complex128:
-            return ACI_C128
-    raise TypeError(f"unsupported dtype {x.dtype}: use float64 or complex128")
+        codes = {np.dtype(np.float64): ACI_R64, np.dtype(np.complex128): ACI_C128,
+                 np.dtype(np.float32): ACI_R32, np.dtype(np.complex64): ACI_C64}
+    if x.dtype in codes:
+        return codes[x.dtype]
+    raise TypeError(f"unsupported dtype {x.dtype}: use float64, complex128, float32 or complex64")
 
 
 class _TTArg:
@@ -249,11 +250,15 @@ class Context:
     # ------------------------------------------------------------ the method
     def elementwise(self, a, b=None, op="mul", tol=1e-10, max_rank=64, *, tol_kind="rel",
                     max_sweeps=20, seed=0, init=None, coef=None, out_memory="device",
-                    pivots=False, profile=False, precision="fp64", pivot_mode="full", overlap="auto"):
+                    pivots=False, profile=False, precision="fp64", pivot_mode="full", overlap="auto",
+                    history=False):
         """y ~ f(a, b) by ACI. ``a``/``b``: lists of cores (torch CUDA tensors, or numpy arrays
-        for host memory). ``precision``: "fp64" or "bf16xS" (S = 2..8 digit planes) for the
-        frame and Pi contractions. ``overlap``: "auto", "off" or "on" (aci_overlap, the schedule
-        of the sweeps). Returns (cores, stats dict)."""
+        for host memory; float64 / complex128, or float32 / complex64 widened by the library).
+        ``precision``: "fp64" or "bf16xS" (S = 2..8 digit planes) for the frame and Pi
+        contractions. ``overlap``: "auto", "off" or "on" (aci_overlap, the schedule of the
+        sweeps). ``history``: record every local update's pivots (aci_stats.hist_*) into
+        info["history"], a dict {(u, b): (rows, cols)} with u = 0 for the initial CI and
+        u = 1 + 2 (i - 1) + h for half-sweep h of iteration i. Returns (cores, stats dict)."""
         import torch
         A = _TTArg(a)
         Bt = _TTArg(b) if b is not None else None
@@ -283,6 +288,14 @@ class Context:
             pcol = (C.c_int32 * (max(L - 1, 1) * max_rank))()
             stats.pivot_rows = C.cast(prow, C.POINTER(C.c_int32))
             stats.pivot_cols = C.cast(pcol, C.POINTER(C.c_int32))
+        if history:
+            nslots, nb = 1 + 2 * int(max_sweeps), max(L - 1, 1)
+            hr = np.full(nslots * nb, -1, dtype=np.int32)
+            hrows = np.full(nslots * nb * max_rank, -1, dtype=np.int32)
+            hcols = np.full(nslots * nb * max_rank, -1, dtype=np.int32)
+            stats.hist_rank = hr.ctypes.data_as(C.POINTER(C.c_int32))
+            stats.hist_rows = hrows.ctypes.data_as(C.POINTER(C.c_int32))
+            stats.hist_cols = hcols.ctypes.data_as(C.POINTER(C.c_int32))
         out = AciTT()
         st = self.lib.aci_elementwise_ex(self.handle, C.byref(A.tt), C.byref(Bt.tt) if Bt else None,
                                          make_op(op, coef), float(tol), int(max_rank), C.byref(opts),
@@ -295,6 +308,12 @@ class Context:
                                   for b in range(L - 1)]
             info["pivot_cols"] = [[int(pcol[b * max_rank + q]) for q in range(info["ranks"][b + 1])]
                                   for b in range(L - 1)]
+        if history:
+            hrows = hrows.reshape(nslots, nb, max_rank)
+            hcols = hcols.reshape(nslots, nb, max_rank)
+            hr = hr.reshape(nslots, nb)
+            info["history"] = {(u, b): (hrows[u, b, :hr[u, b]].copy(), hcols[u, b, :hr[u, b]].copy())
+                               for u in range(nslots) for b in range(L - 1) if hr[u, b] >= 0}
         return cores, info
 
     def _take_output(self, out):
@@ -494,6 +513,20 @@ class Context:
         self._check(self.lib.aci_k_tt_random(self.handle, ACI_C128 if complex_values else ACI_R64,
                                              int(seed), L, d, r, p))
         return cores
+
+    def set_wait_limits(self, exchange_polls=0, pipeline_polls=0):
+        """Bound the device-side waits of later calls to that many polls (0: the defaults)."""
+        self._check(self.lib.aci_set_wait_limits(self.handle, int(exchange_polls), int(pipeline_polls)))
+
+    def fp64_peak(self, blocks=None, iters=4096):
+        """Measured FP64 fused multiply-add throughput of this GPU in TFLOP/s (aci_k_fp64_peak);
+        by default 8 CTAs of 512 threads per SM."""
+        import torch
+        if blocks is None:
+            blocks = 8 * torch.cuda.get_device_properties(self.device).multi_processor_count
+        t = C.c_double()
+        self._check(self.lib.aci_k_fp64_peak(self.handle, int(blocks), int(iters), C.byref(t)))
+        return t.value
 
     def reciprocal(self, x):
         """1/x with the reciprocal of the pivot search (x: float64 CUDA tensor)."""

@@ -72,6 +72,9 @@ struct aci_ctx {
     float* rec_buf = nullptr;
     long long rec_cap = 0;
     unsigned long long* rec_count = nullptr;
+    // diagnostic wait limits (aci_set_wait_limits); 0 = the defaults
+    long long exchange_polls = 0;
+    long long pipeline_polls = 0;
 };
 
 namespace {
@@ -275,6 +278,11 @@ struct Run {
     int** pcol_dev = nullptr;
     int** jprev_dev = nullptr;
 
+    // pivot history of the call (aci_stats.hist_*): one slot per local update and bond
+    bool hist_on = false;
+    int hist_slots = 0;
+    int *hist_rank = nullptr, *hist_rows = nullptr, *hist_cols = nullptr, *hist_iter = nullptr;
+
     static constexpr bool is_cplx = sizeof(T) == sizeof(cplx);
 
     const T* Xp(int n, int s) const { return Xv[n][s]; }
@@ -356,6 +364,12 @@ struct Run {
         if (overlap) {
             for (int n = 0; n < N; ++n) Qb[n] = c.take<T>(qcap);
             Pfull = c.take<T>(pfcap);
+        }
+        if (hist_on) {
+            hist_rank = c.take<int>((size_t)hist_slots * nb);
+            hist_rows = c.take<int>((size_t)hist_slots * nb * chimax);
+            hist_cols = c.take<int>((size_t)hist_slots * nb * chimax);
+            hist_iter = c.take<int>(1);
         }
         Yptr_dev = c.take<T*>(L);
         pcol_dev = c.take<int*>(std::max(nb, 1));
@@ -486,7 +500,7 @@ struct Run {
         cudaEvent_t e = pre(cls);
         if (digits) {
             ck(ctx, aci::launch_gemm_tc<T>(g, Mmax, Nmax, Kmax, digits, tcbuf, tc_bytes, err,
-                                           prof ? kflops + 4 + cls : nullptr, st),
+                                           prof ? kflops + 4 + cls : nullptr, st, ctx->pipeline_polls),
                what);
             ctx->launches++;  // digit split + tensor-core contraction
             kcount[cls]++;
@@ -530,6 +544,7 @@ struct Run {
         }
         a.rook = rook;
         a.no_coop = no_coop;
+        a.spin_limit = ctx->exchange_polls;
         a.tol = tol;
         a.rel = rel;
         a.smax = S;
@@ -544,6 +559,30 @@ struct Run {
         cudaEvent_t e = pre(ACI_KCLASS_PIVOT);
         ck(ctx, aci::launch_prrlu<T>(a, G, st), "prrlu launch");
         post(ACI_KCLASS_PIVOT, e, "prrlu");
+    }
+
+    // Copy the pivots just stored for bond b (rank chi[kidx]) into history slot `slot` (>= 0), or
+    // into the current iteration's half-sweep `half` (slot < 0).
+    void hist(int b, int kidx, int slot, int half) {
+        if (!hist_on) return;
+        aci::HistArgs h;
+        h.chi = chi;
+        h.kidx = kidx;
+        h.prow = prow[b];
+        h.pcol = pcol[b];
+        h.b = b;
+        h.nb = L - 1;
+        h.kstride = chimax;
+        h.nslots = hist_slots;
+        h.slot = slot;
+        h.half = half;
+        h.iter = hist_iter;
+        h.rank = hist_rank;
+        h.rows = hist_rows;
+        h.cols = hist_cols;
+        cudaEvent_t e = pre(ACI_KCLASS_OTHER);
+        aci::launch_hist(h, st);
+        post(ACI_KCLASS_OTHER, e, "pivot history");
     }
 
     // Pi[b] = f(LX[.][b] XR[.][b+1]) with the running max |Pi| (Eq. (pifromframes)).
@@ -644,6 +683,7 @@ struct Run {
         cudaEvent_t e2 = pre(ACI_KCLASS_OTHER);
         aci::launch_map_pivots(chi, b + 1, prow[b], pcol[b], psel_rows, psel_cols, st);
         post(ACI_KCLASS_OTHER, e2, "proposer map");
+        hist(b, b + 1, -1, 0);
     }
 
     void record(int b) {
@@ -906,6 +946,12 @@ struct Run {
         ck(ctx, cudaMemsetAsync(ll, 0, ll_words * sizeof(unsigned long long), st), "clear exchange");
         prrlu_launches = 0;
         ck(ctx, cudaMemsetAsync(gcount, 0, gcount_n * sizeof(int), st), "clear counters");
+        if (hist_on) {  // -1 marks updates that never ran
+            ck(ctx, cudaMemsetAsync(hist_rank, 0xFF, sizeof(int) * hist_slots * nb, st), "history");
+            ck(ctx, cudaMemsetAsync(hist_rows, 0xFF, sizeof(int) * (size_t)hist_slots * nb * chimax, st), "history");
+            ck(ctx, cudaMemsetAsync(hist_cols, 0xFF, sizeof(int) * (size_t)hist_slots * nb * chimax, st), "history");
+            ck(ctx, cudaMemsetAsync(hist_iter, 0, sizeof(int), st), "history");
+        }
         if (pside) {  // the features' side maxima start empty; every features call leaves them so
             static const int kEmpty[4] = {INT_MIN, INT_MIN, INT_MIN, INT_MIN};
             ck(ctx, cudaMemcpyAsync(pside, kEmpty, sizeof(kEmpty), cudaMemcpyHostToDevice, st), "init side maxima");
@@ -1001,6 +1047,7 @@ struct Run {
             gemm(g, ry[s] * d[s], cap[s + 1], ry[s + 1], "init_gemm", ACI_KCLASS_OTHER);
             prrlu(Ms, dimc(ry[s]), dimr(d[s], s + 1), ry[s], d[s] * cap[s + 1], s, s - 1, false,
                   eps_junk, initmax);
+            hist(s - 1, s, 0, 0);
             right_half(s);
         }
         {
@@ -1032,6 +1079,7 @@ struct Run {
                 side_lr(1);
                 if (recording) features(0);
                 prrlu(Pi[0], dimr(d[0], 0), dimr(d[1], 2), mcap[0], ncap[0], 1, 0, false, eps_lr, smax);
+                hist(0, 1, -1, 0);
                 if (recording) record(0);
                 for (int b = 1; b < nb; ++b) {
                     join();
@@ -1042,12 +1090,14 @@ struct Run {
                     if (recording) features(b);
                     prrlu(Pi[b], dimr(d[b], b), dimr(d[b + 1], b + 2), mcap[b], ncap[b], b + 1, b, false,
                           eps_lr + b, smax);
+                    hist(b, b + 1, -1, 0);
                     if (recording) record(b);
                 }
             }
             // right to left: Pi[nb-1] is the full block of the last bond (its frames have not changed)
             prrlu(Pi[nb - 1], dimr(d[nb - 1], nb - 1), dimr(d[nb], nb + 1), mcap[nb - 1], ncap[nb - 1], nb, nb - 1,
                   true, eps_rl + nb - 1, smax);
+            hist(nb - 1, nb, -1, 1);
             for (int b = nb - 2; b >= 0; --b) {
                 join();
                 gather_rl(b);
@@ -1057,11 +1107,17 @@ struct Run {
                 }
                 prrlu(Pi[b], dimr(d[b], b), dimr(d[b + 1], b + 2), mcap[b], ncap[b], b + 1, b, true,
                       eps_rl + b, smax);
+                hist(b, b + 1, -1, 1);
             }
         };
         auto enqueue_iteration = [&]() {
             ck(ctx, cudaMemsetAsync(ll, 0, ll_words * sizeof(unsigned long long), st), "clear exchange");
             prrlu_launches = 0;
+            if (hist_on) {
+                cudaEvent_t e = pre(ACI_KCLASS_OTHER);
+                aci::launch_hist_tick(hist_iter, st);
+                post(ACI_KCLASS_OTHER, e, "pivot history");
+            }
             if (overlap) {
                 enqueue_overlapped();
                 cudaEvent_t e = pre(ACI_KCLASS_OTHER);
@@ -1080,6 +1136,7 @@ struct Run {
                 pi_block(b);
                 prrlu(Pi[b], dimr(d[b], b), dimr(d[b + 1], b + 2), mcap[b], ncap[b], b + 1, b, false,
                       eps_lr + b, smax);
+                hist(b, b + 1, -1, 0);
                 if (recording) record(b);
             }
             for (int b = nb - 1; b >= 0; --b) {  // right to left, CI "left"
@@ -1087,6 +1144,7 @@ struct Run {
                 pi_block(b);
                 prrlu(Pi[b], dimr(d[b], b), dimr(d[b + 1], b + 2), mcap[b], ncap[b], b + 1, b, true,
                       eps_rl + b, smax);
+                hist(b, b + 1, -1, 1);
             }
             cudaEvent_t e = pre(ACI_KCLASS_OTHER);
             aci::launch_iter_check(L, chi, chi_prev, pcol_dev, jprev_dev, eps_lr, eps_rl, smax, err, flags, 0, st);
@@ -1267,6 +1325,12 @@ struct Run {
                 ck(ctx, cudaMemcpy(b.data(), eps_rl, sizeof(double) * (L - 1), cudaMemcpyDeviceToHost), "eps");
                 for (int q = 0; q < L - 1; ++q) stats->eps[q] = std::max(a[q], b[q]);
             }
+            if (hist_on && L > 1) {
+                const size_t nr = (size_t)hist_slots * (L - 1);
+                ck(ctx, cudaMemcpy(stats->hist_rank, hist_rank, sizeof(int) * nr, cudaMemcpyDeviceToHost), "history");
+                ck(ctx, cudaMemcpy(stats->hist_rows, hist_rows, sizeof(int) * nr * chimax, cudaMemcpyDeviceToHost), "history");
+                ck(ctx, cudaMemcpy(stats->hist_cols, hist_cols, sizeof(int) * nr * chimax, cudaMemcpyDeviceToHost), "history");
+            }
             for (int b = 0; b + 1 < L; ++b) {
                 const int k = chi_h[b + 1];
                 if (stats->pivot_rows)
@@ -1283,7 +1347,8 @@ void validate_tt(aci_ctx* ctx, const aci_tt* t, const char* name) {
     if (!t->d || !t->rank || !t->core) fail(ctx, ACI_E_ARG, std::string(name) + ": null array");
     if (t->L < 1) fail(ctx, ACI_E_SHAPE, std::string(name) + ": L < 1");
     if (t->L > 4096) fail(ctx, ACI_E_SHAPE, std::string(name) + ": L > 4096");
-    if (t->dtype != ACI_R64 && t->dtype != ACI_C128) fail(ctx, ACI_E_DTYPE, std::string(name) + ": unsupported dtype");
+    if (t->dtype != ACI_R64 && t->dtype != ACI_C128 && t->dtype != ACI_R32 && t->dtype != ACI_C64)
+        fail(ctx, ACI_E_DTYPE, std::string(name) + ": unsupported dtype");
     if (t->memory != ACI_MEM_DEVICE && t->memory != ACI_MEM_HOST) fail(ctx, ACI_E_ARG, std::string(name) + ": bad memory kind");
     if (t->rank[0] != 1 || t->rank[t->L] != 1) fail(ctx, ACI_E_SHAPE, std::string(name) + ": rank[0] and rank[L] must be 1");
     for (int s = 0; s < t->L; ++s) {
@@ -1291,6 +1356,54 @@ void validate_tt(aci_ctx* ctx, const aci_tt* t, const char* name) {
         if (t->rank[s + 1] < 1 || t->rank[s + 1] > (1 << 20)) fail(ctx, ACI_E_SHAPE, std::string(name) + ": rank out of range");
         if (!t->core[s]) fail(ctx, ACI_E_ARG, std::string(name) + ": null core");
     }
+}
+
+bool complex_dtype(int dt) { return dt == ACI_C128 || dt == ACI_C64; }
+
+// FP32 / complex64 cores widened to FP64 / complex128 copies in one device buffer (released with
+// the object, stream-ordered); FP64 / complex128 TTs pass through untouched.
+struct Widened {
+    aci_ctx* ctx = nullptr;
+    void* buf = nullptr;
+    std::vector<void*> core;
+    aci_tt tt;
+    ~Widened() {
+        if (buf) dev_free(ctx, buf);
+    }
+};
+
+const aci_tt* widen(aci_ctx* ctx, const aci_tt* t, Widened& w) {
+    if (!t || (t->dtype != ACI_R32 && t->dtype != ACI_C64)) return t;
+    const int L = t->L;
+    const size_t per = t->dtype == ACI_C64 ? 2 : 1;  // floats per element
+    std::vector<size_t> off(L + 1, 0), cnt(L, 0);
+    for (int s = 0; s < L; ++s) {
+        cnt[s] = (size_t)t->rank[s] * t->d[s] * t->rank[s + 1] * per;
+        off[s + 1] = off[s] + ((cnt[s] + 31) & ~(size_t)31);
+    }
+    const bool host = t->memory == ACI_MEM_HOST;
+    w.ctx = ctx;
+    w.buf = dev_alloc(ctx, off[L] * sizeof(double) + (host ? off[L] * sizeof(float) : 0));
+    double* dst = static_cast<double*>(w.buf);
+    float* stage = host ? reinterpret_cast<float*>(dst + off[L]) : nullptr;
+    w.core.assign(L, nullptr);
+    for (int s = 0; s < L; ++s) {
+        const float* src = static_cast<const float*>(t->core[s]);
+        if (host) {
+            ck(ctx, cudaMemcpyAsync(stage + off[s], src, cnt[s] * sizeof(float), cudaMemcpyHostToDevice, ctx->stream),
+               "copy FP32 input");
+            src = stage + off[s];
+        }
+        aci::launch_promote(src, (long long)cnt[s], dst + off[s], ctx->stream);
+        ck(ctx, cudaGetLastError(), "widen FP32 input");
+        ctx->launches++;
+        w.core[s] = dst + off[s];
+    }
+    w.tt = *t;
+    w.tt.dtype = t->dtype == ACI_C64 ? ACI_C128 : ACI_R64;
+    w.tt.memory = ACI_MEM_DEVICE;
+    w.tt.core = w.core.data();
+    return &w.tt;
 }
 
 template <class T>
@@ -1316,6 +1429,8 @@ aci_status run_typed(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, 
     R.recording = ctx->rec_buf != nullptr && !R.proposed;
     if (R.proposed && !ctx->prop_params) fail(ctx, ACI_E_ARG, "ACI_PIVOT_PROPOSED needs aci_set_proposer");
     R.seed = o.seed;
+    R.hist_on = stats && stats->hist_rank && stats->hist_rows && stats->hist_cols && a->L > 1;
+    R.hist_slots = 1 + 2 * o.max_sweeps;
     R.op = make_op<T>(op);
     R.init = o.init;
     R.host_in = a->memory == ACI_MEM_HOST;
@@ -1421,20 +1536,25 @@ aci_status aci_elementwise_ex(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, ac
             if (b->dtype != a->dtype) fail(ctx, ACI_E_DTYPE, "a and b differ in dtype");
             if (b->memory != a->memory) fail(ctx, ACI_E_ARG, "a and b differ in memory kind");
         }
-        if (a->dtype == ACI_R64 && op.kind == ACI_OP_AFFINE)
+        if (!complex_dtype(a->dtype) && op.kind == ACI_OP_AFFINE)
             for (int i = 0; i < 4; ++i)
                 if (op.c[i][1] != 0.0) fail(ctx, ACI_E_DTYPE, "complex coefficients on real inputs");
         if (o.init) {
             validate_tt(ctx, o.init, "init");
-            if (o.init->L != a->L || o.init->dtype != a->dtype) fail(ctx, ACI_E_SHAPE, "init differs from the inputs");
+            if (o.init->L != a->L || complex_dtype(o.init->dtype) != complex_dtype(a->dtype))
+                fail(ctx, ACI_E_SHAPE, "init differs from the inputs");
             for (int s = 0; s < a->L; ++s)
                 if (o.init->d[s] != a->d[s]) fail(ctx, ACI_E_SHAPE, "init differs from the inputs in d");
             for (int s = 1; s < a->L; ++s)
                 if (o.init->rank[s] > max_rank) fail(ctx, ACI_E_SHAPE, "init ranks exceed max_rank");
         }
         ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
-        if (a->dtype == ACI_R64) return run_typed<double>(ctx, a, b, op, tol, max_rank, o, out, stats);
-        return run_typed<cplx>(ctx, a, b, op, tol, max_rank, o, out, stats);
+        Widened wa, wb, wi;
+        const aci_tt* A = widen(ctx, a, wa);
+        const aci_tt* B = unary ? b : widen(ctx, b, wb);
+        o.init = widen(ctx, o.init, wi);
+        if (!complex_dtype(A->dtype)) return run_typed<double>(ctx, A, B, op, tol, max_rank, o, out, stats);
+        return run_typed<cplx>(ctx, A, B, op, tol, max_rank, o, out, stats);
     } catch (Fail& f) {
         return f.st;
     } catch (...) {
@@ -1487,6 +1607,8 @@ aci_status aci_elementwise_batch(aci_ctx* ctx, int32_t n, const aci_tt* a, const
             }
             w->own_stream = true;
             w->no_coop = true;
+            w->exchange_polls = ctx->exchange_polls;
+            w->pipeline_polls = ctx->pipeline_polls;
             cudaEvent_t e = nullptr;
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
                 aci_destroy(w);
@@ -1622,7 +1744,8 @@ aci_status aci_k_frame_gemm_prec(aci_ctx* ctx, int32_t dtype, int32_t precision,
             g.chi = dummy;
             g.nprod = 1;
             if (precision) {
-                ck(ctx, aci::launch_gemm_tc<T>(g, M, N, K, precision, tcbuf, tcb, er, nullptr, ctx->stream),
+                ck(ctx, aci::launch_gemm_tc<T>(g, M, N, K, precision, tcbuf, tcb, er, nullptr, ctx->stream,
+                                               ctx->pipeline_polls),
                    "frame_gemm");
                 ctx->launches++;
             } else {
@@ -1716,7 +1839,8 @@ aci_status aci_k_pi_block_prec(aci_ctx* ctx, int32_t dtype, int32_t precision, i
             g.op = make_op<T>(op);
             g.smax = smax;
             if (precision) {
-                ck(ctx, aci::launch_gemm_tc<T>(g, M, N, kmax, precision, tcbuf, tcb, er, nullptr, ctx->stream),
+                ck(ctx, aci::launch_gemm_tc<T>(g, M, N, kmax, precision, tcbuf, tcb, er, nullptr, ctx->stream,
+                                               ctx->pipeline_polls),
                    "pi_block");
                 ctx->launches++;
             } else {
@@ -1809,6 +1933,7 @@ aci_status k_prrlu(aci_ctx* ctx, int rook, int32_t dtype, const void* Min, int32
             a.U = own_lu ? Us : static_cast<T*>(U);
             a.Uld = n;
             a.rook = rook;
+            a.spin_limit = ctx->exchange_polls;
             a.tol = tau;
             a.rel = 0;
             a.W = W;
@@ -1975,6 +2100,51 @@ aci_status aci_k_reciprocal(aci_ctx* ctx, const double* x, int32_t n, double* y)
         ck(ctx, cudaStreamSynchronize(ctx->stream), "reciprocal");
         return ACI_OK;
     } catch (Fail& f) {
+        return f.st;
+    }
+}
+
+aci_status aci_set_wait_limits(aci_ctx* ctx, int64_t exchange_polls, int64_t pipeline_polls) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    if (exchange_polls < 0 || pipeline_polls < 0) {
+        ctx->err = "wait limits must be >= 0";
+        return ACI_E_ARG;
+    }
+    ctx->exchange_polls = exchange_polls;
+    ctx->pipeline_polls = pipeline_polls;
+    for (aci_ctx* w : ctx->workers) {
+        w->exchange_polls = exchange_polls;
+        w->pipeline_polls = pipeline_polls;
+    }
+    return ACI_OK;
+}
+
+aci_status aci_k_fp64_peak(aci_ctx* ctx, int32_t blocks, int32_t iters, double* tflops) {
+    if (!ctx) return ACI_E_ARG;
+    ctx->err.clear();
+    double* dev = nullptr;
+    try {
+        if (!tflops || blocks < 1 || blocks > 65535 || iters < 1 || iters > (1 << 24))
+            fail(ctx, ACI_E_ARG, "bad arguments");
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        dev = static_cast<double*>(dev_alloc(ctx, sizeof(double) * (2 + (size_t)blocks)));
+        const double seed[2] = {1e-3, 0.999999};
+        ck(ctx, cudaMemcpyAsync(dev, seed, sizeof(seed), cudaMemcpyHostToDevice, ctx->stream), "probe seed");
+        aci::launch_fp64_probe(dev, blocks, iters, dev + 2, ctx->stream);  // warm-up
+        note_launch(ctx, "fp64 probe");
+        ck(ctx, cudaEventRecord(ctx->ev0, ctx->stream), "event");
+        aci::launch_fp64_probe(dev, blocks, iters, dev + 2, ctx->stream);
+        note_launch(ctx, "fp64 probe");
+        ck(ctx, cudaEventRecord(ctx->ev1, ctx->stream), "event");
+        ck(ctx, cudaStreamSynchronize(ctx->stream), "fp64 probe");
+        float ms = 0.f;
+        ck(ctx, cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "event time");
+        *tflops = aci::fp64_probe_flops(blocks, iters) / (ms * 1e-3) / 1e12;
+        dev_free(ctx, dev);
+        return ACI_OK;
+    } catch (Fail& f) {
+        if (dev) dev_free(ctx, dev);
         return f.st;
     }
 }

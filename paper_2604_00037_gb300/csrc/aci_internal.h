@@ -57,6 +57,7 @@ template <class T> struct TcArgs {
     unsigned char* planesB;  // [nprod][S][ntiles][ksl] slabs of NT x 16 BF16
     int* expoA;              // [nprod][mtiles * 128] row scale exponents
     int* expoB;              // [nprod][ntiles * NT] column scale exponents
+    long long wait_polls;    // > 0: pipeline waits give up after that many polls (diagnostics); 0: 2 s
 };
 
 struct TcPlan {
@@ -70,7 +71,8 @@ TcPlan tc_plan(int digits, bool cplx_values, int Mmax, int Nmax, int Kmax, int n
 size_t tc_scratch_bytes(const TcPlan& p);
 template <class T>
 cudaError_t launch_gemm_tc(const GemmArgs<T>& g, int Mmax, int Nmax, int Kmax, int digits, void* scratch,
-                           size_t scratch_bytes, int* err, double* tc_flops, cudaStream_t st);
+                           size_t scratch_bytes, int* err, double* tc_flops, cudaStream_t st,
+                           long long wait_polls = 0);
 
 template <class T> struct PrrluArgs {
     const T* Min;       // m x n row-major input, not modified
@@ -98,8 +100,14 @@ template <class T> struct PrrluArgs {
     int* err;           // device error flags (DevErr)
     int rook;           // 1: rook search (W holds prrlu_rook_scratch_elems, ll prrlu_rook_ll_words(G); L, U required)
     int no_coop;        // 1: no cooperative grid launch (the single-cluster kernel at every size)
+    long long spin_limit;  // > 0: exchange waits give up after that many polls (diagnostics); 0: kSpinLimit
     // filled by launch_prrlu
     int epc, wcap_elems, wcap_cols;
+    // Live-shape split between the single-CTA variant and the variant chosen for the capacity:
+    // a block with m <= small_m, n <= small_n and m n <= small_elems is factorised by the single-CTA
+    // kernel and any other by the capacity's variant; each kernel returns at once when the block
+    // is not its own (small_elems = 0: no single-CTA launch).
+    int small_m, small_n, small_elems;
 };
 
 // Target entries of the pivot block per CTA: small blocks run in one CTA (no grid sync).
@@ -237,6 +245,30 @@ template <class T> struct GatherArgs {
     unsigned long long* smax;
 };
 template <class T> void launch_gather(const GatherArgs<T>& a, long long max_elems, int num_sms, cudaStream_t st);
+
+// Pivot history of a call (aci_stats.hist_*): copies chi[kidx] pivots of one local update.
+struct HistArgs {
+    const int* chi;
+    int kidx;
+    const int* prow;
+    const int* pcol;
+    int b, nb, kstride, nslots;
+    int slot;         // >= 0: this slot; < 0: 1 + 2 (*iter - 1) + half
+    int half;
+    const int* iter;  // device iteration counter
+    int* rank;        // [nslots][nb]
+    int* rows;        // [nslots][nb][kstride]
+    int* cols;
+};
+void launch_hist(const HistArgs& h, cudaStream_t st);
+void launch_hist_tick(int* iter, cudaStream_t st);
+
+// dst[e] = (double)src[e] for e < n (FP32 / complex64 inputs widened on load).
+void launch_promote(const float* src, long long n, double* dst, cudaStream_t st);
+
+// FP64 multiply-add throughput probe: `blocks` CTAs of 512 threads, `iters` rounds of the chains.
+double fp64_probe_flops(int blocks, int iters);
+void launch_fp64_probe(const double* seed, int blocks, int iters, double* out, cudaStream_t st);
 
 void launch_iter_check(int L, const int* chi, int* chi_prev, int* const* pcol, int* const* jprev,
                        const double* eps_lr, const double* eps_rl, const unsigned long long* smax,

@@ -181,7 +181,67 @@ __global__ void __launch_bounds__(256) gather_kernel(GatherArgs<T> a) {
     }
 }
 
+// ---------------------------------------------------------------- pivot history (diagnostics)
+// One local update's pivots into the history record: slot h.slot when >= 0, else the slot of
+// half-sweep h.half of the current iteration, 1 + 2 (*iter - 1) + half, with *iter the device
+// iteration counter that hist_tick_kernel advances at the start of every iteration.
+__global__ void hist_kernel(HistArgs h) {
+    const int slot = h.slot >= 0 ? h.slot : 1 + 2 * (*h.iter - 1) + h.half;
+    if (slot < 0 || slot >= h.nslots) return;
+    const int k = h.chi[h.kidx];
+    const size_t u = (size_t)slot * h.nb + h.b;
+    if (threadIdx.x == 0) h.rank[u] = k;
+    for (int q = threadIdx.x; q < k && q < h.kstride; q += blockDim.x) {
+        h.rows[u * h.kstride + q] = h.prow[q];
+        h.cols[u * h.kstride + q] = h.pcol[q];
+    }
+}
+__global__ void hist_tick_kernel(int* iter) { *iter += 1; }
+
+// ---------------------------------------------------------------- FP32 inputs
+// FP32 / complex64 input cores widened to FP64 / complex128 (exact: every float is a double).
+__global__ void promote_kernel(const float* src, long long n, double* dst) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        dst[e] = (double)src[e];
+}
+
+// ---------------------------------------------------------------- FP64 throughput probe
+// Independent chains of FP64 fused multiply-adds per thread: the FP64 pipe's issue rate, the
+// denominator of the FP64 rooflines. The chains are seeded from the inputs and summed into out[]
+// so that no multiply-add can be removed.
+constexpr int kProbeChains = 8;
+__global__ void __launch_bounds__(512) fp64_probe_kernel(const double* seed, int iters, double* out) {
+    double x[kProbeChains];
+    const double a = seed[0], b = seed[1];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) x[c] = a + (double)(threadIdx.x + c);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; ++c) x[c] = fma(x[c], b, a);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; ++c) s += x[c];
+    if (s == 12345.6789) out[blockIdx.x] = s;  // practically never taken; keeps the chains live
+}
+
 }  // namespace
+
+void launch_hist(const HistArgs& h, cudaStream_t st) { hist_kernel<<<1, 256, 0, st>>>(h); }
+void launch_hist_tick(int* iter, cudaStream_t st) { hist_tick_kernel<<<1, 1, 0, st>>>(iter); }
+
+void launch_promote(const float* src, long long n, double* dst, cudaStream_t st) {
+    if (n <= 0) return;
+    const long long nb = std::min<long long>((n + 255) / 256, 4096);
+    promote_kernel<<<(int)nb, 256, 0, st>>>(src, n, dst);
+}
+
+double fp64_probe_flops(int blocks, int iters) {
+    return 2.0 * kProbeChains * 512.0 * (double)blocks * (double)iters;
+}
+void launch_fp64_probe(const double* seed, int blocks, int iters, double* out, cudaStream_t st) {
+    fp64_probe_kernel<<<blocks, 512, 0, st>>>(seed, iters, out);
+}
 
 template <class T>
 void launch_gather(const GatherArgs<T>& a, long long max_elems, int num_sms, cudaStream_t st) {

@@ -12,7 +12,13 @@
 // Limits and sharing:
 //  * The array is kStaticBytes (8 MiB). Every GPU that loads the library holds it until the
 //    process exits. Inputs must satisfy m <= 4096, n <= 4096 and m * n <= 262144; larger
-//    shapes are rejected with ACI_E_SHAPE before anything runs.
+//    shapes are rejected with ACI_E_SHAPE before anything runs. Every shape within these limits
+//    runs: the working copy of the matrix takes at most 4 MiB (m n entries of 8 or 16 bytes), and
+//    when the block is large enough for the cooperative grid variant (more than 2^18 FP64
+//    multiply-adds per step: m n > 2^18 real, > 2^16 complex), its grid is capped so that the
+//    exchange words (2 G (8 + m w) words of 8 bytes, w = 2 real / 4 complex) fit in the rest.
+//    Such a call may therefore run on fewer CTAs than aci_k_prrlu would (same results, as the
+//    pivots and factors do not depend on the grid size).
 //  * Every call on a device uses the same array and leaves its contents behind; each call first
 //    zeroes what must start at zero (the error flag and the words the CTAs exchange at every
 //    pivot step), so stale contents are never read. Calls that overlap on the GPU (two streams,
@@ -32,6 +38,9 @@ constexpr size_t kStaticBytes = size_t(8) << 20;
 constexpr int kMaxDim = 4096;
 constexpr long long kMaxElems = 1LL << 18;
 constexpr int kMaxDevices = 64;
+// FP64 multiply-adds per pivot step above which the pivot search takes the cooperative grid
+// variant (the single-cluster variants use no exchange words); the same bound as launch_prrlu's.
+constexpr long long kGridWork = 1LL << 18;
 
 // The scratch. In host code this name is only a host-side stand-in for the symbol: the device
 // address comes from cudaGetSymbolAddress in static_scratch() below.
@@ -41,14 +50,13 @@ struct StaticDevice {
     bool ready = false;
     unsigned char* base = nullptr;
     int num_sms = 0;
-    unsigned long long calls = 0;
 };
 
 std::mutex g_static_mu;
 StaticDevice g_static_dev[kMaxDevices];
 
 // Once per device (with that device current): resolve and cache the array's device address.
-aci_status static_scratch(int dev, unsigned char** base, int* num_sms, unsigned long long* call_id) {
+aci_status static_scratch(int dev, unsigned char** base, int* num_sms) {
     if (dev < 0 || dev >= kMaxDevices) return ACI_E_ARG;
     std::lock_guard<std::mutex> lock(g_static_mu);
     StaticDevice& s = g_static_dev[dev];
@@ -69,7 +77,6 @@ aci_status static_scratch(int dev, unsigned char** base, int* num_sms, unsigned 
     }
     *base = s.base;
     *num_sms = s.num_sms;
-    *call_id = ++s.calls;  // calls made on this device so far
     return ACI_OK;
 }
 
@@ -94,23 +101,32 @@ aci_status run_static(cudaStream_t st, const void* Min, int m, int n, double tau
     }
     unsigned char* base = nullptr;
     int sms = 0;
-    unsigned long long call_id = 0;
-    aci_status s = static_scratch(dev, &base, &sms, &call_id);
+    aci_status s = static_scratch(dev, &base, &sms);
     if (s != ACI_OK) return s;
-    const int G = aci::prrlu_grid(m, n, sms);
+    const bool cp = sizeof(T) == sizeof(aci::cplx);
     Bump b{base};
     int* k_dev = b.take<int>(1);
     double* eps_dev = b.take<double>(1);
     int* err_dev = b.take<int>(1);
     int* chi_dev = b.take<int>(1);
-    const size_t nll = aci::prrlu_ll_words(m, G, sizeof(T) == sizeof(aci::cplx));
-    unsigned long long* ll = b.take<unsigned long long>(nll);
     T* W = b.take<T>(size_t(m) * n);
-    if (b.off > kStaticBytes) return ACI_E_SHAPE;  // unreachable within the documented limits
+    // The exchange words are used by the cooperative grid variant only (blocks of more than
+    // kGridWork multiply-adds per step); its grid is capped to what the rest of the array holds.
+    int G = 1;
+    size_t nll = 0;
+    unsigned long long* ll = nullptr;
+    if ((long long)m * n * (cp ? 4 : 1) > kGridWork) {
+        G = aci::prrlu_grid(m, n, sms);
+        const size_t room = kStaticBytes - ((b.off + 255) & ~size_t(255));
+        while (G > 1 && aci::prrlu_ll_words(m, G, cp) * sizeof(unsigned long long) > room) --G;
+        nll = aci::prrlu_ll_words(m, G, cp);
+        ll = b.take<unsigned long long>(nll);
+    }
+    if (b.off > kStaticBytes) return ACI_E_SHAPE;  // a shape outside the documented limits
 
     // zero what must start at zero: the error flag and the pivot-search exchange words
     if (cudaMemsetAsync(err_dev, 0, sizeof(int), st) != cudaSuccess ||
-        cudaMemsetAsync(ll, 0, nll * sizeof(unsigned long long), st) != cudaSuccess) {
+        (nll && cudaMemsetAsync(ll, 0, nll * sizeof(unsigned long long), st) != cudaSuccess)) {
         cudaGetLastError();
         return ACI_E_CUDA;
     }

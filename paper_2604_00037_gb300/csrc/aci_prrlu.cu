@@ -23,6 +23,7 @@
 // record, which each does only after it has read the buffer. The caller clears the exchange
 // area once per sequence of launches and gives each launch a distinct tag base.
 // The Schur update of step p is fused with the local argmax of step p+1.
+#include <algorithm>
 #include <climits>
 #include <cstdlib>
 #include <mutex>
@@ -78,9 +79,10 @@ __device__ __forceinline__ void val_of(const unsigned long long* w, cplx& v) {
     v = mkc(dbl_of(w[0], w[1]), dbl_of(w[2], w[3]));
 }
 
-// Read NW consecutive words once all of them carry `tag`; false after the spin limit.
+// Read NW consecutive words once all of them carry `tag`; false after `limit` polls.
 template <int NW>
-__device__ __forceinline__ bool get_words(const unsigned long long* p, unsigned int tag, unsigned long long* out) {
+__device__ __forceinline__ bool get_words(const unsigned long long* p, unsigned int tag, unsigned long long* out,
+                                          long long limit) {
     long long spins = 0;
     for (;;) {
         bool ok = true;
@@ -90,7 +92,7 @@ __device__ __forceinline__ bool get_words(const unsigned long long* p, unsigned 
             ok &= word_tag(out[i]) == tag;
         }
         if (ok) return true;
-        if (++spins > kSpinLimit) return false;
+        if (++spins > limit) return false;
     }
 }
 
@@ -208,12 +210,20 @@ __host__ __device__ inline int live_ctas(long long mn, int n, int G, int epc) {
     return (int)g;
 }
 
+// The live block is the single-CTA kernel's (see PrrluArgs::small_*).
+template <class T>
+__device__ __forceinline__ bool small_block(const PrrluArgs<T>& a, int m, int n) {
+    return a.small_elems > 0 && m <= a.small_m && n <= a.small_n && (long long)m * n <= a.small_elems;
+}
+
 template <class T, bool SMEMW>
 __global__ void __launch_bounds__(PT) prrlu_kernel(PrrluArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int WPV = Words<T>::value;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
     const int m = dimv(a.m, a.chi), n = dimv(a.n, a.chi);
+    if (small_block(a, m, n)) return;  // the single-CTA kernel's block
+    const long long spin_limit = a.spin_limit > 0 ? a.spin_limit : kSpinLimit;
     const int Ge = live_ctas((long long)m * n, n, G, a.epc);
     if (g >= Ge) return;
     const int c0 = (int)(((long long)n * g) / Ge), c1 = (int)(((long long)n * (g + 1)) / Ge);
@@ -299,7 +309,7 @@ __global__ void __launch_bounds__(PT) prrlu_kernel(PrrluArgs<T> a) {
             wlin = INT_MAX;
             if (tid < Ge) {
                 unsigned long long rw[3 + WPV];
-                if (!get_words<3 + WPV>(recs + ((size_t)buf * G + tid) * kRecWords, tag, rw)) {
+                if (!get_words<3 + WPV>(recs + ((size_t)buf * G + tid) * kRecWords, tag, rw, spin_limit)) {
                     atomicOr(a.err, DEVERR_TIMEOUT);
                     sint[0] = 1;
                 } else {
@@ -343,7 +353,7 @@ __global__ void __launch_bounds__(PT) prrlu_kernel(PrrluArgs<T> a) {
             const unsigned long long* wc = cols + ((size_t)buf * G + gw) * (size_t)mmax * WPV;
             for (int r = tid; r < m; r += PT) {
                 unsigned long long cw[WPV];
-                if (!get_words<WPV>(wc + (size_t)r * WPV, tag, cw)) {
+                if (!get_words<WPV>(wc + (size_t)r * WPV, tag, cw, spin_limit)) {
                     atomicOr(a.err, DEVERR_TIMEOUT);
                     sint[1] = 1;
                     break;
@@ -432,6 +442,7 @@ __global__ void __launch_bounds__(PT) prrlu_cluster_kernel(PrrluArgs<T> a) {
     const int g = (int)cl.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m = dimv(a.m, a.chi), n = dimv(a.n, a.chi);
+    if (small_block(a, m, n)) return;  // every CTA of the cluster returns before any exchange
     const int c0 = (int)(((long long)n * g) / C), c1 = (int)(((long long)n * (g + 1)) / C);
     const int w = c1 - c0;
     const int mmax = a.mmax;
@@ -693,6 +704,7 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
     const int g = (int)cl.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m = dimv(a.m, a.chi), n = dimv(a.n, a.chi);
+    if (small_block(a, m, n)) return;  // every CTA of the cluster returns before any exchange
     const int c0 = (int)(((long long)n * g) / C), c1 = (int)(((long long)n * (g + 1)) / C);
     const int w = c1 - c0;  // <= WMAX (the host sizes WMAX for the capacity)
     const int mmax = a.mmax;
@@ -866,6 +878,186 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
         if (a.out_chi_idx >= 0) const_cast<int*>(a.chi)[a.out_chi_idx] = p;
     }
     cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// ---------------------------------------------------------------- single-CTA variant
+// Small live blocks (most bonds of a chain whose ranks fall away from the middle, whatever the
+// capacity the launch was sized for): the whole block in the registers of one CTA of CT threads,
+// so a pivot step needs neither a cluster barrier nor distributed shared memory. Warp w holds the
+// column chunk [w W, w W + W) of every row, lane l the rows l, l + 32, ..., l + 32 (ROWS - 1).
+// Per step: the warp argmax of the per-thread bests (fused in the update) -> shared memory -> one
+// block barrier -> every warp reduces the warp maxima and takes the step's decision itself; the
+// warp holding the pivot column and the lanes holding the pivot row publish them -> a second block
+// barrier -> multipliers, L and U entries and the register update. The arithmetic of every entry
+// is that of the other variants (l = S[r, j] x (1 / pivot), S[r, c] - l S[i, c] fused), so the
+// variants choose the same pivots.
+constexpr int CT = 256;
+constexpr int CWARP = CT / 32;
+
+template <class T, int ROWS, int W>
+__global__ void __launch_bounds__(CT, 1) prrlu_cta_kernel(PrrluArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m = dimv(a.m, a.chi), n = dimv(a.n, a.chi);
+    if (!small_block(a, m, n)) return;  // the capacity's variant takes this block
+
+    // shared memory: lcol[2][32 ROWS] | prow[2][CWARP W] | warp maxima [2][CWARP]
+    T* lcol = reinterpret_cast<T*>(smem_raw);
+    T* prow = lcol + 2 * 32 * ROWS;
+    Cand<T>* wmx = align16<Cand<T>>(prow + 2 * CWARP * W);
+    const int c0 = warp * W;
+
+    T v[ROWS][W];
+    bool live[ROWS];
+    kbits_t bkey = 0;
+    int blin = INT_MAX;
+    T bval = s_zero(T());
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i) {
+        const int r = lane + 32 * i;
+        live[i] = r < m;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            T x = s_zero(T());
+            if (live[i] && c0 + c < n) {
+                x = a.Min[(size_t)r * n + c0 + c];
+                const kbits_t k = key_of(x);
+                const int pos = cpos(r, c0 + c);
+                if (better(k, pos, bkey, blin)) { bkey = k; blin = pos; bval = x; }
+            }
+            v[i][c] = x;
+        }
+    }
+    unsigned int colmask = 0;
+#pragma unroll
+    for (int c = 0; c < W; ++c)
+        if (c0 + c < n) colmask |= 1u << c;
+
+    const int kmax = min(min(m, n), a.chimax);
+    const double S = a.rel ? __longlong_as_double((long long)*a.smax) : 0.0;
+    const double tau = a.rel ? a.tol * S : a.tol;
+
+    int p = 0;
+    double eps = 0.0;
+    for (;;) {
+        const int par = p & 1;
+        int dummy = 0;
+        warp_best(bkey, blin, bval, dummy);
+        if (lane == 0) {
+            Cand<T> mine;
+            mine.key = bkey;
+            mine.lin = blin;
+            mine.pad = 0;
+            mine.val = bval;
+            wmx[par * CWARP + warp] = mine;
+        }
+        __syncthreads();
+        // the step's winner and decision, taken by every warp from the warp maxima
+        kbits_t wk = 0;
+        int wl = INT_MAX, gw = 0;
+        T pv = s_zero(T());
+        if (lane < CWARP) {
+            const Cand<T> c = wmx[par * CWARP + lane];
+            wk = c.key;
+            wl = c.lin;
+            pv = c.val;
+            gw = lane;
+        }
+        warp_best(wk, wl, pv, gw);
+        Decision<T> dl;
+        decide(&dl, wk, wl, pv, p, kmax, tau, false);
+        if (dl.code) {
+            if (dl.code == 2 && tid == 0) atomicOr(a.err, DEVERR_NUMERIC);
+            eps = dl.eps;
+            break;
+        }
+        const int zpiv = dl.zpiv;
+        const int ri = cpos_row(wl), cj = cpos_col(wl);
+        if (tid == 0) {
+            a.piv_rows[p] = ri;
+            a.piv_cols[p] = cj;
+            a.D[p] = pv;
+        }
+        // publish the pivot column (its warp) and the pivot row (its lane in every warp)
+        T* lc = lcol + par * 32 * ROWS;
+        T* pr = prow + par * CWARP * W;
+        if (warp == cj / W) {
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i) lc[lane + 32 * i] = select_reg<T, W>(v[i], cj - c0);
+        }
+        if (lane == (ri & 31)) {
+            const int i0 = ri >> 5;
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+                T x = v[0][c];
+#pragma unroll
+                for (int i = 1; i < ROWS; ++i)
+                    if (i == i0) x = v[i][c];
+                pr[c0 + c] = x;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i)
+            if (lane + 32 * i == ri) live[i] = false;
+        const unsigned oldmask = colmask;
+        if (warp == cj / W) colmask &= ~(1u << (cj - c0));
+        const T inv = zpiv ? s_zero(T()) : recip_of(pv);
+        __syncthreads();
+        T l[ROWS];
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+            const int r = lane + 32 * i;
+            l[i] = (live[i] && !zpiv) ? s_mul(lc[r], inv) : s_zero(T());
+            if (a.L && warp == 0 && r < m) a.L[(size_t)p * a.Lld + r] = (r == ri) ? s_one(T()) : l[i];
+        }
+        if (a.U && lane < W && c0 + lane < n) {  // row p of U over this warp's columns
+            const int c = c0 + lane;
+            T u;
+            if (c == cj) u = s_one(T());
+            else if (!((oldmask >> lane) & 1u) || zpiv) u = s_zero(T());
+            else u = s_mul(pr[c], inv);
+            a.U[(size_t)p * a.Uld + c] = u;
+        }
+        T u[W];
+#pragma unroll
+        for (int c = 0; c < W; ++c) u[c] = pr[c0 + c];
+        // Schur-complement update in registers, fused with the next local argmax (4 chains)
+        kbits_t qk[4] = {0, 0, 0, 0};
+        int ql[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+        T qv[4] = {s_zero(T()), s_zero(T()), s_zero(T()), s_zero(T())};
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+            if (!live[i]) continue;
+            const int rn = cpos(lane + 32 * i, c0);
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+                if ((colmask >> c) & 1u) {
+                    const T x = s_fms(l[i], u[c], v[i][c]);
+                    v[i][c] = x;
+                    const kbits_t k = key_of(x);
+                    if (better(k, rn + c, qk[c & 3], ql[c & 3])) { qk[c & 3] = k; ql[c & 3] = rn + c; qv[c & 3] = x; }
+                }
+            }
+        }
+        bkey = qk[0];
+        blin = ql[0];
+        bval = qv[0];
+#pragma unroll
+        for (int q = 1; q < 4; ++q)
+            if (better(qk[q], ql[q], bkey, blin)) { bkey = qk[q]; blin = ql[q]; bval = qv[q]; }
+        ++p;
+    }
+    if (tid == 0) {
+        if (a.flops) {
+            const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
+            double f = 0.0;
+            for (int q = 0; q < p; ++q) f += (double)(m - q - 1) * (double)(n - q - 1);
+            atomicAdd(a.flops, per * f);
+        }
+        *a.eps_out = eps;
+        if (a.k_out) *a.k_out = p;
+        if (a.out_chi_idx >= 0) const_cast<int*>(a.chi)[a.out_chi_idx] = p;
+    }
 }
 
 // ---------------------------------------------------------------- rook search (second pivot mode)
@@ -1353,10 +1545,90 @@ cudaError_t kernel_attrs(const void* fn) {
 constexpr long long kClusterWorkMax = 1LL << 18;
 constexpr int kCregColsPerCta = 4;
 
+// ACI_PRRLU_CLUSTER: the cluster size of the single-cluster variants (launch-shape tuning only).
+int prrlu_cluster_override() {
+    static const int v = [] {
+        const char* e = std::getenv("ACI_PRRLU_CLUSTER");
+        return e ? std::max(0, std::atoi(e)) : 0;
+    }();
+    return v;
+}
+
+// Live blocks of at most this many entries go to the single-CTA kernel; ACI_PRRLU_SMALL overrides
+// it (0 turns the single-CTA kernel off; launch-shape tuning only: the pivots do not depend on it).
+constexpr int kPrrluSmallElems = 0;
+int prrlu_small_elems() {
+    static const int v = [] {
+        const char* e = std::getenv("ACI_PRRLU_SMALL");
+        return e ? std::max(0, std::atoi(e)) : kPrrluSmallElems;
+    }();
+    return v;
+}
+
+// The single-CTA kernel for capacities up to 32 ROWS x 8 W (ROWS rows per lane, W columns per warp).
+template <class T>
+void (*cta_kernel(int rows, int w))(PrrluArgs<T>) {
+    const bool cp = sizeof(T) == sizeof(cplx);
+    if (rows == 1) {
+        if (w == 4) return prrlu_cta_kernel<T, 1, 4>;
+        if (w == 8) return prrlu_cta_kernel<T, 1, 8>;
+        return prrlu_cta_kernel<T, 1, 16>;
+    }
+    if (rows == 2) {
+        if (w == 4) return prrlu_cta_kernel<T, 2, 4>;
+        if (w == 8) return prrlu_cta_kernel<T, 2, 8>;
+        return prrlu_cta_kernel<T, 2, 16>;
+    }
+    if (!cp) {
+        if constexpr (sizeof(T) == sizeof(double)) {
+            if (w == 4) return prrlu_cta_kernel<T, 4, 4>;
+            if (w == 8) return prrlu_cta_kernel<T, 4, 8>;
+            return prrlu_cta_kernel<T, 4, 16>;
+        }
+    }
+    return nullptr;
+}
+
+// Launch the single-CTA kernel for the live blocks it takes (PrrluArgs::small_*); sets a.small_*.
+// Returns true when it alone covers every live shape of the capacity.
+template <class T>
+cudaError_t launch_small(PrrluArgs<T>& a, cudaStream_t st, bool* covers) {
+    *covers = false;
+    a.small_m = a.small_n = a.small_elems = 0;
+    const int thr = prrlu_small_elems();
+    if (thr <= 0) return cudaSuccess;
+    const bool cp = sizeof(T) == sizeof(cplx);
+    const int mrows = std::min(a.mmax, cp ? 64 : 128), ncols = std::min(a.nmax, 128);
+    const int rows = mrows <= 32 ? 1 : (mrows <= 64 ? 2 : 4);
+    const int w = ncols <= 32 ? 4 : (ncols <= 64 ? 8 : 16);
+    void (*fn)(PrrluArgs<T>) = cta_kernel<T>(rows, w);
+    if (!fn) return cudaSuccess;
+    a.small_m = 32 * rows;
+    a.small_n = CWARP * w;
+    a.small_elems = thr;
+    *covers = a.mmax <= a.small_m && a.nmax <= a.small_n && (long long)a.mmax * a.nmax <= thr;
+    cudaError_t e = kernel_attrs((const void*)fn);
+    if (e != cudaSuccess) return e;
+    size_t smem = sizeof(T) * (2 * 32 * (size_t)rows + 2 * (size_t)CWARP * w);
+    smem = ((smem + 15) & ~(size_t)15) + sizeof(Cand<T>) * 2 * CWARP;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(CT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    return cudaLaunchKernelEx(&cfg, fn, a);
+}
+
 template <class T>
 cudaError_t launch_prrlu(const PrrluArgs<T>& a_in, int G, cudaStream_t st) {
     PrrluArgs<T> a = a_in;
     const bool cp = sizeof(T) == sizeof(cplx);
+    a.small_m = a.small_n = a.small_elems = 0;
+    if (!a.rook) {  // small live blocks: the single-CTA kernel (the others return at once for them)
+        bool covers = false;
+        cudaError_t e = launch_small<T>(a, st, &covers);
+        if (e != cudaSuccess || covers) return e;
+    }
     if (a.rook) {
         // the caller sized W (prrlu_rook_scratch_elems), ll (prrlu_rook_ll_words(G)) and gives L, U
         const int kcap = std::max(1, std::min(std::min(a.mmax, a.nmax), a.chimax));
@@ -1389,6 +1661,7 @@ cudaError_t launch_prrlu(const PrrluArgs<T>& a_in, int G, cudaStream_t st) {
         // 25-35% per launch from 20 x 20 to 200 x 200).
         C = std::max(C, std::min(cmax, (a.nmax + kCregColsPerCta - 1) / kCregColsPerCta));
         C = std::max(1, std::min(C, a.nmax));
+        if (prrlu_cluster_override() > 0) C = std::max(1, std::min(std::min(prrlu_cluster_override(), cmax), a.nmax));
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(C);
         cfg.stream = st;

@@ -84,8 +84,15 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return done != 0;
 }
 
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// polls > 0: give up after that many failed polls (a diagnostic limit, aci_set_wait_limits);
+// 0: after kWaitNs of polling.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, long long polls = 0) {
     if (mbar_try(bar, parity)) return true;
+    if (polls > 0) {
+        for (long long it = 1; it < polls; ++it)
+            if (mbar_try(bar, parity)) return true;
+        return false;
+    }
     const unsigned long long t0 = gtimer();
     for (unsigned it = 1;; ++it) {
         if (mbar_try(bar, parity)) return true;
@@ -328,7 +335,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2) tc_gemm_kernel(TcArgs<T> a) {
     if (warp == 0 && lane == 0) {  // producer: one bulk copy per operand per stage
         for (int c = 0; c < total; ++c) {
             const int st = c % nst, use = c / nst;
-            if (use > 0 && !mbar_wait(bar_empty + 8 * st, (use - 1) & 1)) {
+            if (use > 0 && !mbar_wait(bar_empty + 8 * st, (use - 1) & 1, a.wait_polls)) {
                 *abort_flag = 1;
                 break;
             }
@@ -363,7 +370,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2) tc_gemm_kernel(TcArgs<T> a) {
         for (; c < total; ++c) {
             const int st = c % nst, use = c / nst;
             if (*abort_flag) break;
-            if (!mbar_wait(bar_full + 8 * st, use & 1)) {
+            if (!mbar_wait(bar_full + 8 * st, use & 1, a.wait_polls)) {
                 *abort_flag = 1;
                 break;
             }
@@ -570,7 +577,7 @@ size_t tc_scratch_bytes(const TcPlan& p) { return p.bytesA + p.bytesB + p.bytesE
 
 template <class T>
 cudaError_t launch_gemm_tc(const GemmArgs<T>& g, int Mmax, int Nmax, int Kmax, int digits, void* scratch,
-                           size_t scratch_bytes, int* err, double* tc_flops, cudaStream_t st) {
+                           size_t scratch_bytes, int* err, double* tc_flops, cudaStream_t st, long long wait_polls) {
     if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
     const bool cv = sizeof(T) == sizeof(cplx);
     const TcPlan p = tc_plan(digits, cv, Mmax, Nmax, Kmax, g.nprod, g.combine);
@@ -604,6 +611,7 @@ cudaError_t launch_gemm_tc(const GemmArgs<T>& g, int Mmax, int Nmax, int Kmax, i
     a.ntiles = p.ntiles;
     a.nst = p.nst;
     a.tmem_cols = p.tmem_cols;
+    a.wait_polls = wait_polls;
     unsigned char* base = static_cast<unsigned char*>(scratch);
     a.planesA = base;
     a.planesB = base + p.bytesA;
@@ -626,8 +634,8 @@ cudaError_t launch_gemm_tc(const GemmArgs<T>& g, int Mmax, int Nmax, int Kmax, i
 }
 
 template cudaError_t launch_gemm_tc<double>(const GemmArgs<double>&, int, int, int, int, void*, size_t, int*, double*,
-                                            cudaStream_t);
+                                            cudaStream_t, long long);
 template cudaError_t launch_gemm_tc<cplx>(const GemmArgs<cplx>&, int, int, int, int, void*, size_t, int*, double*,
-                                          cudaStream_t);
+                                          cudaStream_t, long long);
 
 }  // namespace aci

@@ -198,17 +198,19 @@ def sequence_config5_pair(t: int, chi: int, nbits: int = 20, nmodes: int = 200, 
 def batch_config4_spec(seed: int = 1004, n: int = 64):
     """The batched workload: n independent pairs of 2D interleaved Fourier fields as in config 2,
     with lengths L = 2 * nbits, nbits uniform in [10, 20] (L uniform over the even values in
-    [20, 40]), ranks chi uniform in [16, 256], ops alternating a*b and a*conj(b) (the same for
-    real fields). Each field has min(200, chi) modes, enough for its TT-SVD to reach rank chi.
+    [20, 40]), ranks chi uniform in [16, 256], 200 modes per field as in config 2 (TT-SVD
+    truncates each to rank chi), ops alternating a*b and a*conj(b) (the same for real fields),
+    even pairs FP64 and odd pairs FP32 (``dtype``: the element type the pair is handed over in).
     The configuration fixes neither tolerance nor rank cap: tol 1e-8 (relative) and max_rank chi.
-    Returns the per-pair parameters; ``batch_config4_pair`` builds one pair."""
+    Returns the per-pair parameters; ``batch_config4_pair`` builds one pair (in FP64)."""
     rng = np.random.default_rng(seed)
     spec = []
     for i in range(n):
         nbits = int(rng.integers(10, 21))
         chi = int(rng.integers(16, 257))
-        spec.append(dict(index=i, nbits=nbits, chi=chi, nmodes=min(200, chi),
+        spec.append(dict(index=i, nbits=nbits, chi=chi, nmodes=200,
                          op="mul" if i % 2 == 0 else "mul_conj", tol=1e-8, max_rank=chi,
+                         dtype="f64" if i % 2 == 0 else "f32",
                          seed_a=seed * 1000 + 2 * i, seed_b=seed * 1000 + 2 * i + 1))
     return spec
 

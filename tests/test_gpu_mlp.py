@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import mlp
+from synthetic.weights import proposer_init
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +38,7 @@ def cuda(x):
 @pytest.mark.parametrize("n,F", [(1, 1), (17, 7), (1000, 7), (4099, 16)])
 def test_forward_matches_reference(ctx, n, F):
     X, _ = data(n, n, F)
-    p = mlp.init(n + F, F)
+    p = proposer_init(n + F, F)
     assert ctx.mlp_param_count(F) == len(p)
     z = ctx.mlp_forward(cuda(X), cuda(p)).cpu().numpy()
     zr, _ = mlp.forward(p, X, F)
@@ -51,7 +52,7 @@ def test_forward_matches_reference(ctx, n, F):
 @pytest.mark.parametrize("n,F,pw", [(5, 3, 1.0), (777, 7, 3.0), (20000, 9, 1.0)])
 def test_gradient_matches_reference(ctx, n, F, pw):
     X, y = data(100 + n, n, F)
-    p = mlp.init(7, F)
+    p = proposer_init(7, F)
     loss, g = ctx.mlp_grad(cuda(X), cuda(y), cuda(p), pw)
     lr, gr = mlp.loss_grad(p, X, y, F, pw)
     assert loss == pytest.approx(lr, rel=1e-5)
@@ -74,7 +75,7 @@ def test_adam_matches_reference(ctx):
 def test_training_reduces_the_loss(ctx):
     X, y = data(11, 8000, 6)
     Xd, yd = cuda(X), cuda(y)
-    P = cuda(mlp.init(1, 6))
+    P = cuda(proposer_init(1, 6))
     Mt, V = torch.zeros_like(P), torch.zeros_like(P)
     first = None
     for t in range(1, 201):

@@ -1,18 +1,18 @@
 """GPU checks of the overlapped sweep schedule (aci_opts.sweep_overlap): the frame half-products
 and Pi blocks computed over every candidate row or column on a second stream, then gathered after
 each pivot search. The schedule changes only the rounding of the contractions (their K splits),
-so against the oracle it meets the same bar as the plain schedule: identical ranks, iterations and
-pivots where the oracle saw no near-tie, values within 1e-12 of max|y|. Local dimensions 3 and 4
+so against the oracle it meets the same bar as the plain schedule (tests/parity.py): every pivot valid
+against the oracle following it, identical ranks, iterations and final pivots, values within 1e-12
+of max|y|. Local dimensions 3 and 4
 (where the automatic choice keeps the plain schedule) are forced on; the degenerate lengths
 L = 2 (one bond: nothing to overlap) and L = 3 (the shortest overlapped sweep) are included."""
 
 import numpy as np
 import pytest
 
-import oracle
 from synthetic.tt import tt_full, tt_random_uniform
 
-from tests.test_gpu_aci import near_tie_bonds, to_dev, to_np
+from tests.parity import followed_parity, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -36,19 +36,9 @@ def run(ctx, inputs, op, tol, max_rank, overlap, **kw):
 
 
 def check_vs_oracle(ctx, inputs, op, tol, max_rank, overlap="on", coef=None):
-    got, info = run(ctx, inputs, op, tol, max_rank, overlap, coef=coef)
-    ref = oracle.aci(inputs, op, tol, max_rank, coef=coef, record=True)
-    y = to_np(got)
-    ties = near_tie_bonds(ref["log"])
-    if not ties:
-        assert info["ranks"] == ref["ranks"]
-        assert info["iterations"] == ref["iterations"]
-        for b in range(len(inputs[0]) - 1):
-            assert info["pivot_rows"][b] == [int(v) for v in ref["I_pos"][b]], b
-            assert info["pivot_cols"][b] == [int(v) for v in ref["J_pos"][b]], b
-        yr = tt_full(ref["Y"])
-        assert np.abs(tt_full(y) - yr).max() <= 1e-12 * np.abs(yr).max()
-    return y, info, ties
+    """Followed parity (tests/parity.py) in the given schedule; returns (y, info, differ)."""
+    y, info, ref = followed_parity(ctx, inputs, op, tol, max_rank, coef=coef, gpu_kw=dict(overlap=overlap))
+    return y, info, ref["follow"]["differ"]
 
 
 @pytest.mark.parametrize("seed", range(3))
@@ -61,7 +51,7 @@ def test_overlapped_matches_oracle(ctx, seed, d, cplx):
     dt = np.complex128 if cplx else np.float64
     a = tt_random_uniform(rng, L, d, chi, dtype=dt, low=-1, high=1)
     b = tt_random_uniform(rng, L, d, chi, dtype=dt, low=-1, high=1)
-    y, info, ties = check_vs_oracle(ctx, [a, b], "mul", 1e-12, 64)
+    y, info, differ = check_vs_oracle(ctx, [a, b], "mul", 1e-12, 64)
     exact = tt_full(a) * tt_full(b)
     assert np.abs(tt_full(y) - exact).max() <= 1e-9 * np.abs(exact).max()
 
@@ -81,8 +71,8 @@ def test_overlapped_short_chains(ctx, L):
     rng = np.random.default_rng(50 + L)
     a = tt_random_uniform(rng, L, 2, 2, dtype=np.float64, low=-1, high=1)
     b = tt_random_uniform(rng, L, 2, 3, dtype=np.float64, low=-1, high=1)
-    y, info, ties = check_vs_oracle(ctx, [a, b], "mul", 1e-12, 64)
-    assert not ties
+    y, info, differ = check_vs_oracle(ctx, [a, b], "mul", 1e-12, 64)
+    assert differ == 0
 
 
 def test_overlapped_agrees_with_plain_on_a_quantics_field(ctx):

@@ -6,7 +6,7 @@ result within the tolerance of the exact product, as the full right-to-left swee
 import numpy as np
 import pytest
 
-from oracle import mlp
+from synthetic.weights import proposer_init
 from synthetic.tt import tt_full, tt_random_uniform
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +39,7 @@ def pair(seed, L=10, d=2, chi=5, cplx=False):
 def test_keeping_every_candidate_reproduces_plain_aci(ctx, cplx):
     a, b = pair(1, cplx=cplx)
     ref, rinfo = ctx.elementwise(dev(a), dev(b), "mul", 1e-12, 64)
-    ctx.set_proposer(torch.from_numpy(mlp.init(0, 7)).cuda(), keep=1e6)
+    ctx.set_proposer(torch.from_numpy(proposer_init(0, 7)).cuda(), keep=1e6)
     got, info = ctx.elementwise(dev(a), dev(b), "mul", 1e-12, 64, pivot_mode="proposed")
     ctx.set_proposer(None)
     assert info["ranks"] == rinfo["ranks"] and info["iterations"] == rinfo["iterations"]
@@ -67,7 +67,7 @@ def test_trained_proposer_keeps_the_error(ctx):
         a, b = pair(10 + s, L=10, d=2, chi=6)
         ctx.elementwise(dev(a), dev(b), "mul", 1e-10, 64)
     X, y, _ = read()
-    P = torch.from_numpy(mlp.init(3, 7)).cuda()
+    P = torch.from_numpy(proposer_init(3, 7)).cuda()
     M, V = torch.zeros_like(P), torch.zeros_like(P)
     pw = float((1 - y.mean()) / max(y.mean(), 1e-6))
     l0 = None

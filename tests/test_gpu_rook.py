@@ -95,21 +95,13 @@ def test_rook_prrlu_large_complex_cross_interpolates(ctx):
 
 
 def compare_aci(ctx, inputs, op, tol, max_rank, **kw):
-    from tests.test_gpu_aci import near_tie_bonds, to_dev, to_np
-    got, info = ctx.elementwise(*[to_dev(x) for x in inputs], op=op, tol=tol, max_rank=max_rank, pivots=True,
-                                pivot_mode="rook", **kw)
-    ref = oracle.aci(inputs, op, tol, max_rank, record=True, pivot_mode="rook", **kw)
-    y = to_np(got)
-    ties = near_tie_bonds(ref["log"])
-    if not ties:
-        assert info["ranks"] == ref["ranks"]
-        assert info["iterations"] == ref["iterations"]
-        for b in range(len(inputs[0]) - 1):
-            assert info["pivot_rows"][b] == [int(v) for v in ref["I_pos"][b]], b
-            assert info["pivot_cols"][b] == [int(v) for v in ref["J_pos"][b]], b
-        yr = tt_full(ref["Y"])
-        assert np.abs(tt_full(y) - yr).max() <= 1e-12 * np.abs(yr).max()
-    return y, info, ref, ties
+    """Tie-aware whole-call parity in rook mode (tests/parity.py): pivots of every update until the
+    oracle's first near-tie, values always."""
+    from tests.parity import tie_aware_parity
+    gk = dict(pivot_mode="rook")
+    if "seed" in kw:
+        gk["seed"] = kw["seed"]
+    return tie_aware_parity(ctx, inputs, op, tol, max_rank, oracle_kw=dict(pivot_mode="rook", **kw), gpu_kw=gk)
 
 
 @pytest.mark.parametrize("seed", range(4))

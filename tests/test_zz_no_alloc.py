@@ -1,17 +1,25 @@
-"""The allocation-free pivot search (aci_k_prrlu_static) against the regular entry point.
+"""The allocation-free pivot search (aci_k_prrlu_static) against the oracle and the regular entry.
 
 aci_k_prrlu_static serves callers that may not allocate device memory (a host application that
 owns all device memory, a fixed memory budget, code that must not enter an allocator): it runs
-the same pivot search with its scratch in a file-scope device array. This test calls it through
-the C ABI twice in a row, on two different matrices, and checks each result against
-aci_k_prrlu on the same input, with the tolerances of the other pivot-search tests. It lives in
-a file collected last so that a stop-at-first-failure run has run every other test first.
+the same pivot search with its scratch in a file-scope device array. These tests call it through
+the C ABI several times in a row, on matrices at the corners of its documented limits (4096 x 64
+and 64 x 4096 real, 512 x 512 complex, 4096 x 64 complex) and on blocks that take each pivot-search
+variant (the 16-CTA register kernel, the shared-memory cluster kernel, the cooperative grid
+kernel), and check each result against the oracle's Algorithm 2 (tests/test_gpu_kernels.py's
+comparison, pivots exact up to the first near-tie) and against aci_k_prrlu on the same input. A
+second pair of calls checks that the calls allocate nothing: torch's allocator counters and the
+device's free memory are unchanged across them. The file is collected last so that a
+stop-at-first-failure run has run every other test first.
 """
 
 import ctypes as C
 
 import numpy as np
 import pytest
+
+import oracle
+from tests.test_gpu_kernels import _compare_prrlu
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -28,14 +36,14 @@ def env():
     ctx.close()
 
 
-def _static_prrlu(lib, binding, M, tau, chimax):
+def _static_prrlu(lib, binding, M, tau, chimax, outs=None):
     m, n = M.shape
     kc = min(m, n, chimax)
-    pr = torch.empty(kc, dtype=torch.int32, device=M.device)
-    pc = torch.empty(kc, dtype=torch.int32, device=M.device)
-    D = torch.empty(kc, dtype=M.dtype, device=M.device)
-    Lm = torch.zeros((kc, m), dtype=M.dtype, device=M.device)
-    Um = torch.zeros((kc, n), dtype=M.dtype, device=M.device)
+    if outs is None:
+        outs = (torch.empty(kc, dtype=torch.int32, device=M.device), torch.empty(kc, dtype=torch.int32, device=M.device),
+                torch.empty(kc, dtype=M.dtype, device=M.device), torch.zeros((kc, m), dtype=M.dtype, device=M.device),
+                torch.zeros((kc, n), dtype=M.dtype, device=M.device))
+    pr, pc, D, Lm, Um = outs
     k = C.c_int32()
     eps = C.c_double()
     stream = torch.cuda.current_stream().cuda_stream
@@ -48,9 +56,9 @@ def _static_prrlu(lib, binding, M, tau, chimax):
                 eps=eps.value, L=Lm[:kk].T.cpu().numpy(), U=Um[:kk].cpu().numpy())
 
 
-def _matrix(seed, m, n, cplx):
+def _matrix(seed, m, n, cplx, rank=None):
     rng = np.random.default_rng(seed)
-    r = min(m, n)
+    r = min(m, n) if rank is None else rank
     U = rng.standard_normal((m, r))
     V = rng.standard_normal((r, n))
     if cplx:
@@ -59,27 +67,63 @@ def _matrix(seed, m, n, cplx):
     return (U * (10.0 ** -np.linspace(0, 10, r))) @ V
 
 
-def _same(got, ref, scale):
+CASES = [  # (m, n, complex, taurel, chimax): in call order
+    (300, 200, False, 0.0, 150),     # register kernel
+    (64, 96, True, 1e-8, 40),        # register kernel, complex
+    (300, 300, True, 1e-8, 120),     # complex, 4 m n > 2^18: the cooperative grid kernel
+    (4096, 64, False, 1e-10, 64),    # corner m = 4096 real: cluster kernel, block in shared memory
+    (64, 4096, False, 1e-10, 64),    # corner n = 4096 real
+    (512, 512, True, 1e-10, 96),     # corner m n = 2^18 complex: grid kernel, grid capped by the array
+    (4096, 64, True, 1e-10, 64),     # corner m = 4096 complex: grid kernel, grid capped by the array
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_static_prrlu_matches_oracle_and_regular_entry(env, case):
+    lib, ctx, binding = env
+    m, n, cplx, taurel, chimax = CASES[case]
+    M = _matrix(100 + case, m, n, cplx, rank=min(m, n, 160))
+    Md = torch.from_numpy(M).cuda()
+    tau = taurel * np.abs(M).max()
+    got = _static_prrlu(lib, binding, Md, tau, chimax)
+    _compare_prrlu(got, oracle.ldu(M, tau, chimax), M)
+    ref = ctx.prrlu(Md, tau, chimax)
     assert got["k"] == ref["k"]
     assert list(got["I"]) == list(ref["I"]) and list(got["J"]) == list(ref["J"])
-    assert abs(got["eps"] - ref["eps"]) <= 1e-12 * scale
-    np.testing.assert_allclose(got["D"], ref["D"], atol=1e-12 * scale, rtol=1e-12)
-    bound = 1e-13 * scale / np.abs(ref["D"]) + 1e-12
-    assert (np.abs(got["L"] - ref["L"]) <= bound[None, :]).all()
-    assert (np.abs(got["U"] - ref["U"]) <= bound[:, None]).all()
+    assert np.array_equal(got["D"], ref["D"])
 
 
-def test_static_prrlu_matches_regular_entry_two_calls_in_a_row(env):
+def test_static_prrlu_two_calls_in_a_row_allocate_nothing(env):
     lib, ctx, binding = env
-    cases = [(_matrix(1, 300, 200, False), 0.0, 150),     # first call: real, larger
-             (_matrix(2, 64, 96, True), 1e-8, 40)]         # second call: complex, smaller
-    for M, taurel, chimax in cases:
-        Md = torch.from_numpy(M).cuda()
-        scale = np.abs(M).max()
-        tau = taurel * scale
-        got = _static_prrlu(lib, binding, Md, tau, chimax)
-        ref = ctx.prrlu(Md, tau, chimax)
-        _same(got, ref, scale)
+    M1 = torch.from_numpy(_matrix(1, 300, 300, True)).cuda()
+    M2 = torch.from_numpy(_matrix(2, 64, 96, False)).cuda()
+    tau2 = 1e-9 * float(M2.abs().max())
+    o1 = (torch.empty(96, dtype=torch.int32, device="cuda"), torch.empty(96, dtype=torch.int32, device="cuda"),
+          torch.empty(96, dtype=torch.complex128, device="cuda"),
+          torch.zeros((96, 300), dtype=torch.complex128, device="cuda"),
+          torch.zeros((96, 300), dtype=torch.complex128, device="cuda"))
+    o2 = (torch.empty(40, dtype=torch.int32, device="cuda"), torch.empty(40, dtype=torch.int32, device="cuda"),
+          torch.empty(40, dtype=torch.float64, device="cuda"), torch.zeros((40, 64), dtype=torch.float64, device="cuda"),
+          torch.zeros((40, 96), dtype=torch.float64, device="cuda"))
+    # warm-up of both shapes: the first call sets up the array's address, and each kernel's first
+    # launch may load its module
+    _static_prrlu(lib, binding, M1, 0.0, 96, o1)
+    _static_prrlu(lib, binding, M2, tau2, 40, o2)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    free0, _ = torch.cuda.mem_get_info()
+    a = _static_prrlu(lib, binding, M1, 0.0, 96, o1)
+    b = _static_prrlu(lib, binding, M2, tau2, 40, o2)
+    torch.cuda.synchronize()
+    after = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    free1, _ = torch.cuda.mem_get_info()
+    assert after == before  # no device allocation through torch's allocator
+    assert free1 == free0   # nor any other device allocation
+    r1 = ctx.prrlu(M1, 0.0, 96)
+    r2 = ctx.prrlu(M2, tau2, 40)
+    assert list(a["I"]) == list(r1["I"]) and list(a["J"]) == list(r1["J"])
+    assert list(b["I"]) == list(r2["I"]) and list(b["J"]) == list(r2["J"])
+    np.testing.assert_array_equal(b["D"], r2["D"])
 
 
 def test_static_prrlu_rejects_sizes_beyond_its_array(env):
