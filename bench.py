@@ -73,6 +73,13 @@ def parse():
     ap.add_argument("--proposer", action="store_true",
                     help="the learned-proposal sequence: train on steps 0-39, compare on 40-59")
     ap.add_argument("--seq-steps", type=int, default=60)
+    ap.add_argument("--scaling", action="store_true", help="time vs chi on the paper's scaling workloads")
+    ap.add_argument("--scaling-fourier", default="64,256,1024,4096,16384,32768", help="K values (Sec. 3.2)")
+    ap.add_argument("--scaling-random", default="8,16,32,64,128,256", help="chi values (Sec. 3.3)")
+    ap.add_argument("--scaling-sweeps", type=int, default=2, help="sweeps of the random-TT products (tol 0)")
+    ap.add_argument("--scaling-cpu-chi", type=int, default=256, help="largest input chi the CPU oracle's ACI runs")
+    ap.add_argument("--scaling-kron-chi", type=int, default=32, help="largest input chi of the CPU Kronecker product")
+    ap.add_argument("--scaling-fit-from", type=int, default=64, help="smallest chi in the GPU fits")
     ap.add_argument("--keep", default="1.25",
                     help="proposer: kept candidates per side = keep x previous rank + 8; a comma list compares several")
     return ap.parse_args()
@@ -194,6 +201,122 @@ def run_batch(args):
     line = {"metric": "batched ACI products/s (independent pairs of uneven L and chi)", "higher_is_better": True,
             "dtype": "f64 (odd pairs handed over in FP32)", "data": "synthetic", "n_gpus": 1, "steps": args.steps,
             **line}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def _scaling_input(job):
+    """One input of the scaling workloads (in a worker process): ("fourier", seed, K) or
+    ("random", seed, chi)."""
+    kind, seed, x = job
+    if kind == "fourier":
+        from synthetic.fields import fourier_paper_1d_large
+        return fourier_paper_1d_large(seed, x)[0]
+    import numpy as np
+    from synthetic.tt import tt_random_uniform
+    return tt_random_uniform(np.random.default_rng(seed), 30, 2, x)
+
+
+def _oracle_time(job):
+    """Wall time of one CPU product (in a one-thread worker): ("aci" | "kron", a, b, tol, max_rank, sweeps)."""
+    kind, a, b, tol, max_rank, sweeps = job
+    t0 = time.perf_counter()
+    if kind == "aci":
+        import oracle
+        oracle.aci([a, b], "mul", tol, max_rank, maxiter=sweeps, tol_kind="abs" if tol > 0 else "rel")
+    else:
+        from oracle.hadamard import hadamard_kron, tt_round_svd
+        tt_round_svd(hadamard_kron(a, b), max_rank=max_rank, rel_tol=tol)
+    return time.perf_counter() - t0
+
+
+def _fit(xs, ts):
+    import numpy as np
+    if len(xs) < 2:
+        return None
+    p, c = np.polyfit(np.log(np.asarray(xs, float)), np.log(np.asarray(ts, float)), 1)
+    return float(p)
+
+
+def run_scaling(args):
+    """Time vs chi on the paper's scaling workloads, FP64 / complex128 on one GPU, with fitted
+    power laws t ~ chi^p (Sec. 3.2: products of two random Fourier series, 1D quantics L = 30,
+    tol 1e-8, the ranks set by the tolerance; Sec. 3.3: products of uniform random TTs, L = 30,
+    d = 2, output rank capped at chi' = chi). Beside them, on one CPU thread each, the oracle's
+    ACI and the O(chi^4) Kronecker-delta product with SVD rounding where they finish in seconds."""
+    import multiprocessing as mp
+    import numpy as np
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    Ks = [int(k) for k in args.scaling_fourier.split(",") if k]
+    chis = [int(c) for c in args.scaling_random.split(",") if c]
+    jobs = [("fourier", s, K) for K in Ks for s in (3001, 3002)] + [("random", s, c) for c in chis for s in (3003, 3004)]
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:  # before any GPU call
+        made = pool.map(_scaling_input, jobs)
+        inputs = {(j[0], j[2]): [] for j in jobs}
+        for j, tt in zip(jobs, made):
+            inputs[(j[0], j[2])].append(tt)
+        cpu_jobs, cpu_keys = [], []
+        for (kind, x), (a, b) in inputs.items():
+            chi = max(c.shape[2] for c in a)
+            tol, mr, sw = (1e-8, 4096, args.max_sweeps) if kind == "fourier" else (0.0, x, args.scaling_sweeps)
+            if chi <= args.scaling_cpu_chi and (kind == "random" or chi <= 64):
+                cpu_jobs += [("aci", a, b, tol, mr, sw)]
+                cpu_keys += [(kind, x, "aci")]
+            if chi <= args.scaling_kron_chi:
+                cpu_jobs += [("kron", a, b, tol, mr, sw)]
+                cpu_keys += [(kind, x, "kron")]
+        cpu_times = dict(zip(cpu_keys, pool.map(_oracle_time, cpu_jobs)))
+    gen_s = time.time() - t0
+    import torch
+    from paper_2604_00037_gb300.binding import Context
+    from synthetic.tt import tt_eval
+    ctx = Context(0)
+    stream = torch.cuda.current_stream()
+    rows = {"fourier": [], "random": []}
+    rng = np.random.default_rng(21)
+    for (kind, x), (a, b) in inputs.items():
+        A, B = [torch.from_numpy(c).cuda() for c in a], [torch.from_numpy(c).cuda() for c in b]
+        tol, mr, sw = (1e-8, 4096, args.max_sweeps) if kind == "fourier" else (0.0, x, args.scaling_sweeps)
+        # Sec. 3.2's tau is absolute (the paper's Alg. 1); the random-TT products run at a rank cap
+        call = lambda: ctx.elementwise(A, B, "mul", tol, mr, max_sweeps=sw, tol_kind="abs" if tol > 0 else "rel")
+        call()
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            y, info = call()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        pts = rng.integers(0, 2, size=(1000, len(a)))  # the paper samples 10^3 points
+        exact = tt_eval(a, pts) * tt_eval(b, pts)
+        diff = float(np.abs(tt_eval([c.cpu().numpy() for c in y], pts) - exact).max())
+        chi = max(c.shape[2] for c in a)
+        row = {"x": x, "chi": chi, "chi_out": max(info["ranks"]), "sweeps": info["iterations"],
+               "gpu_ms": statistics.median(ts), "max_abs_err": diff, "max_rel_err": diff / float(np.abs(exact).max()),
+               "oracle_aci_s": cpu_times.get((kind, x, "aci")), "oracle_kron_s": cpu_times.get((kind, x, "kron"))}
+        rows[kind].append(row)
+        print(json.dumps({kind: row}), file=sys.stderr, flush=True)
+    fits = {}
+    for kind, rr in rows.items():
+        rr.sort(key=lambda r: r["chi"])
+        big = [r for r in rr if r["chi"] >= args.scaling_fit_from]
+        cpu = [r for r in rr if r["chi"] >= 16]
+        fits[kind] = {"gpu": _fit([r["chi"] for r in big], [r["gpu_ms"] for r in big]),
+                      "oracle_aci": _fit([r["chi"] for r in cpu if r["oracle_aci_s"]], [r["oracle_aci_s"] for r in cpu if r["oracle_aci_s"]]),
+                      "oracle_kron": _fit([r["chi"] for r in cpu if r["oracle_kron_s"]], [r["oracle_kron_s"] for r in cpu if r["oracle_kron_s"]])}
+    line = {"metric": "ACI product time vs chi (paper's scaling workloads), fitted exponent p of t ~ chi^p",
+            "unit": "ms/product", "dtype": "complex128 (Fourier) / f64 (random)", "data": "synthetic", "n_gpus": 1,
+            "config": {"fourier": f"Sec. 3.2: two random Fourier series of K+1 modes, K in {Ks}, 1D quantics L = 30, "
+                                  f"a*b, absolute tau 1e-8 as in the paper, <= {args.max_sweeps} sweeps",
+                       "random": f"Sec. 3.3: uniform random TTs, L = 30, d = 2, chi in {chis}, chi' <= chi (tol 0), "
+                                 f"{args.scaling_sweeps} sweeps",
+                       "fit": f"least squares on log t vs log chi over chi >= {args.scaling_fit_from} (GPU) and over "
+                              f"chi >= 16 (CPU)", "cpu": "one thread per product", "input_generation_s": gen_s},
+            "fourier": rows["fourier"], "random": rows["random"], "exponents": fits,
+            "paper_exponents": {"aci": 2.3, "kron": 3.8, "source": "Sec. 3.2, Fig. 2 (single CPU thread, context only)"}}
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -651,6 +774,8 @@ def main():
         return run_batch(args)
     if args.proposer:
         return run_proposer(args)
+    if args.scaling:
+        return run_scaling(args)
     import numpy as np
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -2,7 +2,7 @@
  * aci.h - C ABI of the GB300 library for alternating cross interpolation (ACI).
  *
  * ACI (arXiv:2604.00037, Sec. 2 and Algorithm 1) computes a tensor train (TT) y with
- * y[sigma] ~ f(x^1[sigma], ..., x^N[sigma]) for an elementwise function f of N <= 2 input
+ * y[sigma] ~ f(x^1[sigma], ..., x^N[sigma]) for an elementwise function f of N <= 4 input
  * TTs, in O(chi^3) per bond instead of the O(chi^4) of a Kronecker-delta contraction.
  * Every step of the sweep runs in the library's own CUDA kernels on one GPU.
  *
@@ -230,6 +230,16 @@ aci_status aci_elementwise(aci_ctx *ctx, const aci_tt *a, const aci_tt *b, aci_o
 aci_status aci_elementwise_ex(aci_ctx *ctx, const aci_tt *a, const aci_tt *b, aci_op op,
                               double tol, int32_t max_rank, const aci_opts *opts,
                               aci_tt *out, aci_stats *stats);
+
+/* y ~ f(x^1, ..., x^n) for n = 1..4 inputs (Sec. 2.1: the method takes N input TTs): the call of
+ * aci_elementwise_ex with the input list as an array. n = 1 takes ACI_OP_ABS2_MUL, n = 2 any op
+ * (inputs[0] = a, inputs[1] = b), n = 3 or 4 the product of all inputs, ACI_OP_MUL
+ * (f = x^1 x^2 ... x^n, multiplied left to right). Each input has its own frames and Pi block
+ * (Eq. (pifromframes)); f combines the n blocks entrywise. The inputs share L, d, dtype and
+ * memory kind. For n > 2 the contractions run in FP64 (ACI_PREC_FP64) and ACI_PIVOT_PROPOSED is
+ * not available (ACI_E_ARG). Outputs, options and diagnostics are those of aci_elementwise_ex. */
+aci_status aci_elementwise_n(aci_ctx *ctx, int32_t n, const aci_tt *inputs, aci_op op, double tol,
+                             int32_t max_rank, const aci_opts *opts, aci_tt *out, aci_stats *stats);
 
 /* Independent products in one call (no counterpart in the paper: a throughput form of
  * aci_elementwise_ex for many pairs of uneven length and rank). Product i is

@@ -68,11 +68,15 @@ OPS = ("mul", "mul_conj", "abs2_mul", "affine")
 
 
 def apply_op(op: str, xs, coef=None):
-    """f(x^1, ..., x^N) entrywise: a*b, a*conj(b), |a|^2 a, or c0 + c1 a + c2 b + c3 a b."""
+    """f(x^1, ..., x^N) entrywise: a*b, a*conj(b), |a|^2 a, or c0 + c1 a + c2 b + c3 a b; for
+    N > 2 inputs "mul" is the product of all of them, taken left to right."""
     a = xs[0]
     b = xs[1] if len(xs) > 1 else None
     if op == "mul":
-        return a * b
+        out = a * b
+        for x in xs[2:]:
+            out = out * x
+        return out
     if op == "mul_conj":
         return a * np.conj(b)
     if op == "abs2_mul":

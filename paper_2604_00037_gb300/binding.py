@@ -79,7 +79,8 @@ EXPORTS = ["aci_create", "aci_destroy", "aci_last_error", "aci_opts_default", "a
            "aci_k_frame_gemm_prec", "aci_k_pi_block_prec", "aci_k_prrlu", "aci_k_prrlu_rook",
            "aci_k_tt_random", "aci_k_apply_pinv", "aci_k_prrlu_static", "aci_k_reciprocal",
            "aci_k_mlp_param_count", "aci_k_mlp_forward", "aci_k_mlp_grad", "aci_k_mlp_adam",
-           "aci_set_proposer", "aci_set_proposer_record", "aci_k_fp64_peak", "aci_set_wait_limits"]
+           "aci_set_proposer", "aci_set_proposer_record", "aci_k_fp64_peak", "aci_set_wait_limits",
+           "aci_elementwise_n"]
 
 _lib = None
 
@@ -110,6 +111,8 @@ def load_library(build_if_missing: bool = True) -> C.CDLL:
     lib.aci_elementwise_ex.argtypes = [vp, C.POINTER(AciTT), C.POINTER(AciTT), AciOp, dbl, i32,
                                        C.POINTER(AciOpts), C.POINTER(AciTT), C.POINTER(AciStats)]
     lib.aci_tt_release.argtypes = [vp, C.POINTER(AciTT)]
+    lib.aci_elementwise_n.argtypes = [vp, i32, C.POINTER(AciTT), AciOp, dbl, i32, C.POINTER(AciOpts),
+                                      C.POINTER(AciTT), C.POINTER(AciStats)]
     lib.aci_elementwise_batch.argtypes = [vp, i32, C.POINTER(AciTT), C.POINTER(AciTT), C.POINTER(AciOp),
                                           C.POINTER(dbl), C.POINTER(i32), C.POINTER(AciOpts), C.POINTER(AciTT),
                                           C.POINTER(AciStats), C.POINTER(i32)]
@@ -254,14 +257,21 @@ class Context:
                     history=False):
         """y ~ f(a, b) by ACI. ``a``/``b``: lists of cores (torch CUDA tensors, or numpy arrays
         for host memory; float64 / complex128, or float32 / complex64 widened by the library).
+        ``a`` may instead be a list of 1-4 input TTs (``b`` None): aci_elementwise_n, where 3 or 4
+        inputs take op "mul" (the product of all).
         ``precision``: "fp64" or "bf16xS" (S = 2..8 digit planes) for the frame and Pi
         contractions. ``overlap``: "auto", "off" or "on" (aci_overlap, the schedule of the
         sweeps). ``history``: record every local update's pivots (aci_stats.hist_*) into
         info["history"], a dict {(u, b): (rows, cols)} with u = 0 for the initial CI and
         u = 1 + 2 (i - 1) + h for half-sweep h of iteration i. Returns (cores, stats dict)."""
         import torch
-        A = _TTArg(a)
-        Bt = _TTArg(b) if b is not None else None
+        extra = None
+        if isinstance(a, (list, tuple)) and a and isinstance(a[0], (list, tuple)):
+            extra = [_TTArg(x) for x in a]  # several inputs (aci_elementwise_n)
+            A, Bt = extra[0], None
+        else:
+            A = _TTArg(a)
+            Bt = _TTArg(b) if b is not None else None
         opts = AciOpts()
         self.lib.aci_opts_default(C.byref(opts))
         opts.tol_kind = TOL_KINDS[tol_kind]
@@ -297,9 +307,14 @@ class Context:
             stats.hist_rows = hrows.ctypes.data_as(C.POINTER(C.c_int32))
             stats.hist_cols = hcols.ctypes.data_as(C.POINTER(C.c_int32))
         out = AciTT()
-        st = self.lib.aci_elementwise_ex(self.handle, C.byref(A.tt), C.byref(Bt.tt) if Bt else None,
-                                         make_op(op, coef), float(tol), int(max_rank), C.byref(opts),
-                                         C.byref(out), C.byref(stats))
+        if extra is not None:
+            arr = (AciTT * len(extra))(*[x.tt for x in extra])
+            st = self.lib.aci_elementwise_n(self.handle, len(extra), arr, make_op(op, coef), float(tol),
+                                            int(max_rank), C.byref(opts), C.byref(out), C.byref(stats))
+        else:
+            st = self.lib.aci_elementwise_ex(self.handle, C.byref(A.tt), C.byref(Bt.tt) if Bt else None,
+                                             make_op(op, coef), float(tol), int(max_rank), C.byref(opts),
+                                             C.byref(out), C.byref(stats))
         self._check(st)
         cores = self._take_output(out)
         info = self._info(st, stats, ranks, eps, L)

@@ -187,7 +187,7 @@ struct Run {
     size_t pcand = 1;          // largest mcap + ncap
     int overlap_opt = ACI_OVERLAP_AUTO;
     int overlap = 0;           // overlapped schedule (aci_overlap) in effect
-    T* Qb[2] = {nullptr, nullptr};  // half-products over all candidate rows / columns
+    T* Qb[aci::kMaxInputs] = {};    // half-products over all candidate rows / columns
     T* Pfull = nullptr;             // Pi over all candidate rows / columns
     size_t qcap = 1, pfcap = 1;
     // per-kernel-class accounting (aci_kernel_class)
@@ -247,13 +247,13 @@ struct Run {
     std::vector<int> cap, ry;              // [L+1]
     std::vector<int> mcap, ncap, kcap;     // per bond
     bool host_in = false;
-    const aci_tt* in[2] = {nullptr, nullptr};
+    const aci_tt* in[aci::kMaxInputs] = {};
     const aci_tt* init = nullptr;
 
     // device buffers
-    std::vector<const T*> Xv[2];
-    std::vector<T*> Xcopy[2];
-    std::vector<T*> LX[2], XR[2], Yinit, Ysc, Pi, D, Lm, Um;
+    std::vector<const T*> Xv[aci::kMaxInputs];
+    std::vector<T*> Xcopy[aci::kMaxInputs];
+    std::vector<T*> LX[aci::kMaxInputs], XR[aci::kMaxInputs], Yinit, Ysc, Pi, D, Lm, Um;
     std::vector<int*> prow, pcol, jprev;
     T* Minit[2] = {nullptr, nullptr};
     int *chi = nullptr, *chi_prev = nullptr, *dd = nullptr, *err = nullptr;
@@ -1407,15 +1407,15 @@ const aci_tt* widen(aci_ctx* ctx, const aci_tt* t, Widened& w) {
 }
 
 template <class T>
-aci_status run_typed(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, double tol, int32_t max_rank,
+aci_status run_typed(aci_ctx* ctx, int N, const aci_tt* const* ins, aci_op op, double tol, int32_t max_rank,
                      const aci_opts& o, aci_tt* out, aci_stats* stats) {
     Run<T> R;
+    const aci_tt* a = ins[0];
     R.ctx = ctx;
     R.st = ctx->stream;
     R.L = a->L;
-    R.N = (op.kind == ACI_OP_ABS2_MUL) ? 1 : 2;
-    R.in[0] = a;
-    R.in[1] = (R.N == 2) ? b : nullptr;
+    R.N = N;
+    for (int n = 0; n < N; ++n) R.in[n] = ins[n];
     R.chimax = max_rank;
     R.tol = tol;
     R.rel = o.tol_kind == ACI_TOL_REL;
@@ -1426,7 +1426,7 @@ aci_status run_typed(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, 
     R.no_coop = ctx->no_coop ? 1 : 0;
     R.proposed = o.pivot_mode == ACI_PIVOT_PROPOSED ? 1 : 0;
     R.overlap_opt = o.sweep_overlap;
-    R.recording = ctx->rec_buf != nullptr && !R.proposed;
+    R.recording = ctx->rec_buf != nullptr && !R.proposed && N <= 2;  // the proposer's features take <= 2 inputs
     if (R.proposed && !ctx->prop_params) fail(ctx, ACI_E_ARG, "ACI_PIVOT_PROPOSED needs aci_set_proposer");
     R.seed = o.seed;
     R.hist_on = stats && stats->hist_rank && stats->hist_rows && stats->hist_cols && a->L > 1;
@@ -1505,13 +1505,20 @@ void aci_opts_default(aci_opts* o) {
     o->out_memory = ACI_MEM_DEVICE;
 }
 
-aci_status aci_elementwise_ex(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, double tol, int32_t max_rank,
+namespace {
+// The inputs x^1..x^N of one call (N = 1 for ACI_OP_ABS2_MUL, 2 for the other binary ops, up to
+// kMaxInputs for the product of aci_elementwise_n): validation, FP32 widening, dispatch.
+aci_status elementwise_inputs(aci_ctx* ctx, int N, const aci_tt* const* ins, aci_op op, double tol, int32_t max_rank,
                               const aci_opts* opts, aci_tt* out, aci_stats* stats) {
     if (!ctx) return ACI_E_ARG;
     ctx->err.clear();
     try {
-        if (!a || !out) fail(ctx, ACI_E_ARG, "a and out must not be NULL");
+        if (!out) fail(ctx, ACI_E_ARG, "out must not be NULL");
+        if (N < 1 || N > aci::kMaxInputs) fail(ctx, ACI_E_ARG, "1 to 4 inputs");
+        for (int n = 0; n < N; ++n)
+            if (!ins[n]) fail(ctx, ACI_E_ARG, n == 0 ? "a must not be NULL" : "b must not be NULL for a binary op");
         if (op.kind < ACI_OP_MUL || op.kind > ACI_OP_AFFINE) fail(ctx, ACI_E_ARG, "unknown op kind");
+        if (N > 2 && op.kind != ACI_OP_MUL) fail(ctx, ACI_E_ARG, "more than two inputs: the op must be ACI_OP_MUL");
         if (!(tol >= 0.0) || !(tol < INFINITY)) fail(ctx, ACI_E_ARG, "tol must be finite and >= 0");
         if (max_rank < 1 || max_rank > 8190) fail(ctx, ACI_E_ARG, "max_rank must be in [1, 8190]");
         aci_opts o;
@@ -1522,19 +1529,24 @@ aci_status aci_elementwise_ex(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, ac
         if (o.pivot_mode != ACI_PIVOT_FULL && o.pivot_mode != ACI_PIVOT_ROOK && o.pivot_mode != ACI_PIVOT_PROPOSED)
             fail(ctx, ACI_E_ARG, "unsupported pivot mode");
         if (!valid_precision(o.precision)) fail(ctx, ACI_E_ARG, "unsupported precision");
+        if (N > 2 && o.precision != ACI_PREC_FP64)
+            fail(ctx, ACI_E_ARG, "more than two inputs: the contractions run in FP64 only");
+        if (N > 2 && o.pivot_mode == ACI_PIVOT_PROPOSED) fail(ctx, ACI_E_ARG, "the proposer takes at most two inputs");
         if (o.sweep_overlap < ACI_OVERLAP_AUTO || o.sweep_overlap > ACI_OVERLAP_ON)
             fail(ctx, ACI_E_ARG, "unsupported sweep_overlap");
         if (o.out_memory != ACI_MEM_DEVICE && o.out_memory != ACI_MEM_HOST) fail(ctx, ACI_E_ARG, "bad out_memory");
+        const aci_tt* a = ins[0];
         validate_tt(ctx, a, "a");
-        const bool unary = op.kind == ACI_OP_ABS2_MUL;
-        if (!unary) {
-            if (!b) fail(ctx, ACI_E_ARG, "b must not be NULL for a binary op");
-            validate_tt(ctx, b, "b");
-            if (b->L != a->L) fail(ctx, ACI_E_SHAPE, "a and b differ in L");
+        for (int n = 1; n < N; ++n) {
+            const aci_tt* b = ins[n];
+            const char* nm = N == 2 ? "b" : "input";
+            validate_tt(ctx, b, nm);
+            if (b->L != a->L) fail(ctx, ACI_E_SHAPE, N == 2 ? "a and b differ in L" : "the inputs differ in L");
             for (int s = 0; s < a->L; ++s)
-                if (a->d[s] != b->d[s]) fail(ctx, ACI_E_SHAPE, "a and b differ in d");
-            if (b->dtype != a->dtype) fail(ctx, ACI_E_DTYPE, "a and b differ in dtype");
-            if (b->memory != a->memory) fail(ctx, ACI_E_ARG, "a and b differ in memory kind");
+                if (a->d[s] != b->d[s]) fail(ctx, ACI_E_SHAPE, N == 2 ? "a and b differ in d" : "the inputs differ in d");
+            if (b->dtype != a->dtype) fail(ctx, ACI_E_DTYPE, N == 2 ? "a and b differ in dtype" : "the inputs differ in dtype");
+            if (b->memory != a->memory)
+                fail(ctx, ACI_E_ARG, N == 2 ? "a and b differ in memory kind" : "the inputs differ in memory kind");
         }
         if (!complex_dtype(a->dtype) && op.kind == ACI_OP_AFFINE)
             for (int i = 0; i < 4; ++i)
@@ -1549,18 +1561,45 @@ aci_status aci_elementwise_ex(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, ac
                 if (o.init->rank[s] > max_rank) fail(ctx, ACI_E_SHAPE, "init ranks exceed max_rank");
         }
         ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
-        Widened wa, wb, wi;
-        const aci_tt* A = widen(ctx, a, wa);
-        const aci_tt* B = unary ? b : widen(ctx, b, wb);
+        Widened w[aci::kMaxInputs], wi;
+        const aci_tt* X[aci::kMaxInputs] = {};
+        for (int n = 0; n < N; ++n) X[n] = widen(ctx, ins[n], w[n]);
         o.init = widen(ctx, o.init, wi);
-        if (!complex_dtype(A->dtype)) return run_typed<double>(ctx, A, B, op, tol, max_rank, o, out, stats);
-        return run_typed<cplx>(ctx, A, B, op, tol, max_rank, o, out, stats);
+        if (!complex_dtype(X[0]->dtype)) return run_typed<double>(ctx, N, X, op, tol, max_rank, o, out, stats);
+        return run_typed<cplx>(ctx, N, X, op, tol, max_rank, o, out, stats);
     } catch (Fail& f) {
         return f.st;
     } catch (...) {
         ctx->err = "unexpected host exception";
         return ACI_E_ARG;
     }
+}
+}  // namespace
+
+aci_status aci_elementwise_ex(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, double tol, int32_t max_rank,
+                              const aci_opts* opts, aci_tt* out, aci_stats* stats) {
+    const aci_tt* ins[2] = {a, b};
+    return elementwise_inputs(ctx, op.kind == ACI_OP_ABS2_MUL ? 1 : 2, ins, op, tol, max_rank, opts, out, stats);
+}
+
+aci_status aci_elementwise_n(aci_ctx* ctx, int32_t n, const aci_tt* inputs, aci_op op, double tol, int32_t max_rank,
+                             const aci_opts* opts, aci_tt* out, aci_stats* stats) {
+    if (!ctx) return ACI_E_ARG;
+    if (!inputs || n < 1 || n > aci::kMaxInputs) {
+        ctx->err = "inputs must hold 1 to 4 TTs";
+        return ACI_E_ARG;
+    }
+    const aci_tt* ins[aci::kMaxInputs] = {};
+    for (int i = 0; i < n; ++i) ins[i] = &inputs[i];
+    if (n <= 2 && op.kind == ACI_OP_ABS2_MUL && n != 1) {
+        ctx->err = "ACI_OP_ABS2_MUL takes one input";
+        return ACI_E_ARG;
+    }
+    if (n == 1 && op.kind != ACI_OP_ABS2_MUL) {
+        ctx->err = "one input: the op must be ACI_OP_ABS2_MUL";
+        return ACI_E_ARG;
+    }
+    return elementwise_inputs(ctx, n, ins, op, tol, max_rank, opts, out, stats);
 }
 
 aci_status aci_elementwise(aci_ctx* ctx, const aci_tt* a, const aci_tt* b, aci_op op, double tol, int32_t max_rank,

@@ -125,6 +125,17 @@ __device__ __forceinline__ T apply_f(const OpParams<T>& op, T a, T b) {
     }
 }
 
+// f of n inputs (n >= 1): apply_f for n <= 2; for more inputs the library's only op is the
+// product of all of them, formed left to right as the oracle does.
+constexpr int kMaxInputs = 4;
+template <class T>
+__device__ __forceinline__ T apply_fn(const OpParams<T>& op, const T* v, int n) {
+    if (n <= 2) return apply_f(op, v[0], n > 1 ? v[1] : v[0]);
+    T r = s_mul(v[0], v[1]);
+    for (int i = 2; i < n; ++i) r = s_mul(r, v[i]);
+    return r;
+}
+
 // ---------------------------------------------------------------- device-resolved shapes
 // A dimension that depends on the ranks chosen on the device: value = mul * chi[idx]
 // (or mul when idx < 0). chi[] is the device array of output ranks chi[0..L].

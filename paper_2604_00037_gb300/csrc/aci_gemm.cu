@@ -37,11 +37,11 @@ __device__ __forceinline__ cplx ldcg_t(const cplx* p) {
 }
 
 struct Plan {
-    int M[2], N[2], K[2];
-    int tiles[2];  // output tiles per product (combine: one shared output)
-    int kc;        // K chunks per product
+    int M[kMaxInputs], N[kMaxInputs], K[kMaxInputs];
+    int tiles[kMaxInputs];  // output tiles per product (combine: one shared output)
+    int kc;                 // K chunks per product
     int units;
-    int nout;      // outputs (combine: 1)
+    int nout;               // outputs (combine: 1)
 };
 
 template <class T>
@@ -49,7 +49,7 @@ __device__ __forceinline__ Plan make_plan(const GemmArgs<T>& g) {
     Plan pl;
     const int nq = g.nprod;
     int maxkc = 1, tiles_total = 0;
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < kMaxInputs; ++q) {
         pl.M[q] = pl.N[q] = pl.K[q] = 0;
         pl.tiles[q] = 0;
     }
@@ -92,8 +92,9 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
     }
 
     for (int u = blockIdx.x; u < pl.units; u += gridDim.x) {
-        // decode the unit: (output o, tile t, product q, K chunk c)
-        int o, t, q, c;
+        // decode the unit: (output o, tile t, product q, K chunk c); tile_base / unit_base: the
+        // tiles and units of the outputs before o
+        int o, t, q, c, tile_base = 0, unit_base = 0;
         if (g.combine) {
             o = 0;
             t = u % pl.tiles[0];
@@ -101,9 +102,13 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
             c = rest % pl.kc;
             q = rest / pl.kc;
         } else {
-            const int per0 = pl.tiles[0] * pl.kc;
-            o = (u < per0) ? 0 : 1;
-            const int uu = o == 0 ? u : u - per0;
+            o = 0;
+            while (o + 1 < pl.nout && u - unit_base >= pl.tiles[o] * pl.kc) {
+                unit_base += pl.tiles[o] * pl.kc;
+                tile_base += pl.tiles[o];
+                ++o;
+            }
+            const int uu = u - unit_base;
             t = uu % pl.tiles[o];
             c = uu / pl.tiles[o];
             q = o;
@@ -155,9 +160,8 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
             __syncthreads();
         }
         // partial tile -> scratch slot (q, c, t) of output o
-        const int tile_id = (o == 0 ? 0 : pl.tiles[0]) + t;
-        const int slot = (g.combine ? (q * pl.kc + c) * pl.tiles[0] + t : (o == 0 ? c * pl.tiles[0] + t
-                                                                              : pl.tiles[0] * pl.kc + c * pl.tiles[1] + t));
+        const int tile_id = tile_base + t;
+        const int slot = g.combine ? (q * pl.kc + c) * pl.tiles[0] + t : unit_base + c * pl.tiles[o] + t;
         T* part = g.part + (size_t)slot * (BM * BN);
 #pragma unroll
         for (int i = 0; i < TM; ++i)
@@ -181,16 +185,18 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
                 const int lc = tx * TN + j, gc = n0 + lc;
                 T v;
                 if (g.combine) {
-                    T s[2] = {s_zero(T()), s_zero(T())};
-                    for (int qq = 0; qq < nq; ++qq)
+                    T s[kMaxInputs];
+                    for (int qq = 0; qq < nq; ++qq) {
+                        s[qq] = s_zero(T());
                         for (int cc = 0; cc < pl.kc; ++cc)
                             s[qq] = s_add(s[qq], ldcg_t(g.part + (size_t)((qq * pl.kc + cc) * pl.tiles[0] + t) * (BM * BN) +
                                                              lr * BN + lc));
-                    v = apply_f(g.op, s[0], s[1]);
+                    }
+                    v = apply_fn(g.op, s, nq);
                 } else {
                     v = s_zero(T());
                     for (int cc = 0; cc < pl.kc; ++cc) {
-                        const int sl = (o == 0) ? cc * pl.tiles[0] + t : pl.tiles[0] * pl.kc + cc * pl.tiles[1] + t;
+                        const int sl = unit_base + cc * pl.tiles[o] + t;
                         v = s_add(v, ldcg_t(g.part + (size_t)sl * (BM * BN) + lr * BN + lc));
                     }
                 }

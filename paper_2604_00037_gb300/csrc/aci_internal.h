@@ -8,11 +8,11 @@ namespace aci {
 // C = gather_rows(A) * gather_cols(B) (batch: one output per product) or
 // C[0] = f(A^0 B^0, A^1 B^1) (combine). Row-major everything; ldc = N.
 template <class T> struct GemmArgs {
-    const T* A[2];
-    const T* B[2];
-    T* C[2];
-    DimE M[2], N[2];
-    DimE K[2], lda[2], ldb[2];
+    const T* A[kMaxInputs];
+    const T* B[kMaxInputs];
+    T* C[kMaxInputs];
+    DimE M[kMaxInputs], N[kMaxInputs];
+    DimE K[kMaxInputs], lda[kMaxInputs], ldb[kMaxInputs];
     const int* arow;  // optional row gather of A (shared by the products)
     const int* bcol;  // optional column gather of B
     const int* chi;   // device rank array the DimE refer to
@@ -225,7 +225,7 @@ struct IterFlags {
     double S;
 };
 // Gathers of the overlapped sweep: dst[r * dld + c] = src[gather_row(r) * sld + gather_col(c)]
-// for r < rows, c < cols (shapes read on the device), up to three independent jobs per launch.
+// for r < rows, c < cols (shapes read on the device), up to 1 + kMaxInputs independent jobs per launch.
 // One job may also fold max |dst| into *smax (bits of a non-negative double, as the contractions).
 template <class T> struct GatherJob {
     const T* src;
@@ -236,7 +236,7 @@ template <class T> struct GatherJob {
     const int* cidx;  // see gather_col
     DimE cblk, cstride;
 };
-constexpr int kGatherJobs = 3;
+constexpr int kGatherJobs = 1 + kMaxInputs;
 template <class T> struct GatherArgs {
     GatherJob<T> job[kGatherJobs];
     int njobs;

@@ -829,7 +829,8 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
 #pragma unroll
         for (int i = 0; i < ROWS; ++i) {
             const int r = tid + i * RT;
-            l[i] = s_mul(wv[i], inv);
+            l[i] = s_zero(T());
+            if (live[i]) l[i] = s_mul(wv[i], inv);  // no FP64 issue for warps whose rows are all used
             if (a.L && r >= r0 && r < r1) a.L[(size_t)p * a.Lld + r] = (r == ri) ? s_one(T()) : l[i];
         }
         if (a.U && tid < w) {  // row p of U for the own columns, one thread per column
@@ -901,10 +902,11 @@ __global__ void __launch_bounds__(CT, 1) prrlu_cta_kernel(PrrluArgs<T> a) {
     const int m = dimv(a.m, a.chi), n = dimv(a.n, a.chi);
     if (!small_block(a, m, n)) return;  // the capacity's variant takes this block
 
-    // shared memory: lcol[2][32 ROWS] | prow[2][CWARP W] | warp maxima [2][CWARP]
+    // shared memory: lcol[2][32 ROWS] | prow[2][CWARP W] | 1 / pivot [2] | warp maxima [2][CWARP]
     T* lcol = reinterpret_cast<T*>(smem_raw);
     T* prow = lcol + 2 * 32 * ROWS;
-    Cand<T>* wmx = align16<Cand<T>>(prow + 2 * CWARP * W);
+    T* sinv = prow + 2 * CWARP * W;
+    Cand<T>* wmx = align16<Cand<T>>(sinv + 2);
     const int c0 = warp * W;
 
     T v[ROWS][W];
@@ -1001,13 +1003,17 @@ __global__ void __launch_bounds__(CT, 1) prrlu_cta_kernel(PrrluArgs<T> a) {
             if (lane + 32 * i == ri) live[i] = false;
         const unsigned oldmask = colmask;
         if (warp == cj / W) colmask &= ~(1u << (cj - c0));
-        const T inv = zpiv ? s_zero(T()) : recip_of(pv);
+        // one thread forms the reciprocal (FP64 issue slots are scarce: 2 multiply-adds per clock
+        // per SM), the block barrier below publishes it
+        if (tid == 0) sinv[par] = zpiv ? s_zero(T()) : recip_of(pv);
         __syncthreads();
+        const T inv = sinv[par];
         T l[ROWS];
 #pragma unroll
         for (int i = 0; i < ROWS; ++i) {
             const int r = lane + 32 * i;
-            l[i] = (live[i] && !zpiv) ? s_mul(lc[r], inv) : s_zero(T());
+            l[i] = s_zero(T());
+            if (live[i] && !zpiv) l[i] = s_mul(lc[r], inv);
             if (a.L && warp == 0 && r < m) a.L[(size_t)p * a.Lld + r] = (r == ri) ? s_one(T()) : l[i];
         }
         if (a.U && lane < W && c0 + lane < n) {  // row p of U over this warp's columns
@@ -1556,7 +1562,7 @@ int prrlu_cluster_override() {
 
 // Live blocks of at most this many entries go to the single-CTA kernel; ACI_PRRLU_SMALL overrides
 // it (0 turns the single-CTA kernel off; launch-shape tuning only: the pivots do not depend on it).
-constexpr int kPrrluSmallElems = 0;
+constexpr int kPrrluSmallElems = 4096;
 int prrlu_small_elems() {
     static const int v = [] {
         const char* e = std::getenv("ACI_PRRLU_SMALL");
@@ -1589,8 +1595,8 @@ void (*cta_kernel(int rows, int w))(PrrluArgs<T>) {
     return nullptr;
 }
 
-// Launch the single-CTA kernel for the live blocks it takes (PrrluArgs::small_*); sets a.small_*.
-// Returns true when it alone covers every live shape of the capacity.
+// Launch the single-CTA kernel when its capacity covers the launch's (PrrluArgs::small_*); *covers
+// tells whether it did.
 template <class T>
 cudaError_t launch_small(PrrluArgs<T>& a, cudaStream_t st, bool* covers) {
     *covers = false;
@@ -1603,13 +1609,16 @@ cudaError_t launch_small(PrrluArgs<T>& a, cudaStream_t st, bool* covers) {
     const int w = ncols <= 32 ? 4 : (ncols <= 64 ? 8 : 16);
     void (*fn)(PrrluArgs<T>) = cta_kernel<T>(rows, w);
     if (!fn) return cudaSuccess;
+    // Only when the kernel covers every live shape of the capacity: a second, gated launch per
+    // pivot search costs more (several microseconds of launch latency) than it saves.
+    if (!(a.mmax <= 32 * rows && a.nmax <= CWARP * w && (long long)a.mmax * a.nmax <= thr)) return cudaSuccess;
     a.small_m = 32 * rows;
     a.small_n = CWARP * w;
     a.small_elems = thr;
-    *covers = a.mmax <= a.small_m && a.nmax <= a.small_n && (long long)a.mmax * a.nmax <= thr;
+    *covers = true;
     cudaError_t e = kernel_attrs((const void*)fn);
     if (e != cudaSuccess) return e;
-    size_t smem = sizeof(T) * (2 * 32 * (size_t)rows + 2 * (size_t)CWARP * w);
+    size_t smem = sizeof(T) * (2 * 32 * (size_t)rows + 2 * (size_t)CWARP * w + 2);
     smem = ((smem + 15) & ~(size_t)15) + sizeof(Cand<T>) * 2 * CWARP;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(1);

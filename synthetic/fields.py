@@ -150,6 +150,25 @@ def fourier_paper_1d(seed: int, K: int, L: int = 30, rel_tol: float = 1e-12):
     return cores, dict(g=g)
 
 
+def fourier_paper_1d_large(seed: int, K: int, L: int = 30, chunk: int = 256, rel_tol: float = 1e-12):
+    """fourier_paper_1d for large K: the same coefficients; the modes are summed in chunks of
+    ``chunk`` consecutive frequencies (each chunk a block sum rounded by TT-SVD), and the chunks
+    are then added pairwise with TT-SVD rounding after every sum, so no block sum is wider than
+    twice the series' own rank."""
+    rng = np.random.default_rng(seed)
+    g = rng.uniform(0, 1, K + 1) + 1j * rng.uniform(0, 1, K + 1)
+    g = g / np.sqrt((np.abs(g) ** 2).sum())
+    parts = []
+    for k0 in range(0, K + 1, chunk):
+        modes = [exp_mode_tt(g[k], _site_angles([k], L, 1, "1d", 1.0)) for k in range(k0, min(K + 1, k0 + chunk))]
+        parts.append(tt_svd_round(tt_block_sum(modes), rel_tol=rel_tol))
+    while len(parts) > 1:
+        nxt = [tt_svd_round(tt_block_sum(parts[i:i + 2]), rel_tol=rel_tol) if i + 1 < len(parts) else parts[i]
+               for i in range(0, len(parts), 2)]
+        parts = nxt
+    return parts[0], dict(g=g)
+
+
 def gaussian_pair(L: int, w: float, delta: float, rel_tol: float = 1e-15):
     """Sec. 3.1, Eq. (gaussians): g_pm(x) = exp(-(x pm delta/2)^2 / (2 w^2)) on x in [-0.5, 0.5),
     as TT-SVD of the dense 2^L-point vectors."""

@@ -162,3 +162,15 @@ def test_warm_start_from_previous_output():
     r2 = oracle.aci([a, b], "mul", 1e-10, 64, init=r1["Y"])
     assert r2["iterations"] <= r1["iterations"]
     assert rel_err(tt_full(r2["Y"]), tt_full(a) * tt_full(b)) <= 1e-9
+
+
+def test_three_and_four_inputs_reproduce_the_dense_product():
+    """N > 2 inputs (Sec. 2.1, f of x^1..x^N): the product of three or four random low-rank TTs is
+    reproduced exactly (its rank, the product of the input ranks, fits under the cap)."""
+    rng = np.random.default_rng(31)
+    for N, chi in ((3, 2), (4, 2)):
+        ins = [tt_random_uniform(rng, 7, 2, chi, low=-1, high=1) for _ in range(N)]
+        r = oracle.aci(ins, "mul", 1e-13, 64)
+        exact = np.prod([tt_full(x) for x in ins], axis=0)
+        assert np.abs(tt_full(r["Y"]) - exact).max() <= 1e-12 * np.abs(exact).max()
+        assert max(r["ranks"]) <= chi ** N
