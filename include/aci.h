@@ -126,6 +126,13 @@ typedef struct {
                               products per 16 SMs (the width of one pivot-search cluster) on
                               successive calls, timing each, then keeps the fastest          */
     int32_t sweep_overlap; /* aci_overlap: schedule of the sweeps (results agree to rounding)    */
+    int32_t autotune;      /* 1: before its sweeps, a call times the FP64 contraction's split-K
+                              granularity (1, 2, 4 or 8 work units per SM) on every shape class it
+                              will launch (capacity buckets of M, N, K; products; Pi or frame form)
+                              that the context has not tuned yet, and keeps the fastest in the
+                              context for this and later calls; results are unchanged except for
+                              the summation order of the contractions. 0 (default): 4 per SM  */
+    int32_t _pad2;
 } aci_opts;
 
 /* Schedule of the sweeps (aci_opts.sweep_overlap). The frame half-products and the Pi block of a

@@ -39,7 +39,7 @@ class AciOpts(C.Structure):
     _fields_ = [("tol_kind", C.c_int32), ("max_sweeps", C.c_int32), ("pivot_mode", C.c_int32),
                 ("precision", C.c_int32), ("seed", C.c_uint64), ("init", C.POINTER(AciTT)),
                 ("out_memory", C.c_int32), ("profile", C.c_int32), ("batch_streams", C.c_int32),
-                ("sweep_overlap", C.c_int32)]
+                ("sweep_overlap", C.c_int32), ("autotune", C.c_int32), ("_pad2", C.c_int32)]
 
 
 class AciStats(C.Structure):
@@ -254,7 +254,7 @@ class Context:
     def elementwise(self, a, b=None, op="mul", tol=1e-10, max_rank=64, *, tol_kind="rel",
                     max_sweeps=20, seed=0, init=None, coef=None, out_memory="device",
                     pivots=False, profile=False, precision="fp64", pivot_mode="full", overlap="auto",
-                    history=False):
+                    history=False, autotune=False):
         """y ~ f(a, b) by ACI. ``a``/``b``: lists of cores (torch CUDA tensors, or numpy arrays
         for host memory; float64 / complex128, or float32 / complex64 widened by the library).
         ``a`` may instead be a list of 1-4 input TTs (``b`` None): aci_elementwise_n, where 3 or 4
@@ -282,6 +282,7 @@ class Context:
         opts.precision = _precision_code(precision)
         opts.pivot_mode = PIVOT_MODES[pivot_mode]
         opts.sweep_overlap = OVERLAP_MODES[overlap]
+        opts.autotune = 1 if autotune else 0
         It = None
         if init is not None:
             It = _TTArg(init)
@@ -365,7 +366,8 @@ class Context:
                              for i, k in enumerate(KERNEL_CLASSES)})
 
     def elementwise_batch(self, items, *, tol_kind="rel", max_sweeps=20, seed=0, out_memory="device",
-                          precision="fp64", pivot_mode="full", streams=0, profile=False, overlap="auto"):
+                          precision="fp64", pivot_mode="full", streams=0, profile=False, overlap="auto",
+                          autotune=False):
         """Independent products in one call. ``items``: list of dicts with keys a, b (None for
         abs2_mul), op, tol, max_rank (and optional coef). Returns a list of (cores, info) with
         info["status"] per product; raises only for call-level errors."""
@@ -388,6 +390,7 @@ class Context:
         opts.pivot_mode = PIVOT_MODES[pivot_mode]
         opts.batch_streams = int(streams)
         opts.sweep_overlap = OVERLAP_MODES[overlap]
+        opts.autotune = 1 if autotune else 0
         outs = (AciTT * max(n, 1))()
         stats = (AciStats * max(n, 1))()
         keep = []

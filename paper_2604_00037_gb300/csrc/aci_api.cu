@@ -75,6 +75,8 @@ struct aci_ctx {
     // diagnostic wait limits (aci_set_wait_limits); 0 = the defaults
     long long exchange_polls = 0;
     long long pipeline_polls = 0;
+    // split-K granularity per contraction shape class, from the tuner of aci_opts.autotune
+    std::map<unsigned long long, int> gemm_units;
 };
 
 namespace {
@@ -278,6 +280,12 @@ struct Run {
     int** pcol_dev = nullptr;
     int** jprev_dev = nullptr;
 
+    // contraction tuner (aci_opts.autotune): the shape classes this call launches
+    int autotune = 0;
+    struct GemmShape {
+        int M, N, K, nprod, combine;
+    };
+    std::vector<GemmShape> gemm_shapes;
     // pivot history of the call (aci_stats.hist_*): one slot per local update and bond
     bool hist_on = false;
     int hist_slots = 0;
@@ -435,7 +443,9 @@ struct Run {
             for (int s = 0; s <= L; ++s) rmax = std::max(rmax, r[n][s]);
         for (int s = 0; s <= L; ++s) rmax = std::max(rmax, ry[s]);
         // optional: a contraction of the overlapped schedule, which falls back to the plain one
+        gemm_shapes.clear();
         auto need = [&](int Mm, int Nm, int nprod, int combine, bool optional = false) {
+            gemm_shapes.push_back({Mm, Nm, rmax, nprod, combine});
             if (digits) {  // K of every contraction is an input rank or an initial-guess rank
                 const aci::TcPlan p = aci::tc_plan(digits, is_cplx, Mm, Nm, rmax, nprod, combine);
                 if (!p.ok) {
@@ -488,6 +498,98 @@ struct Run {
         }
     }
 
+    // ---------------------------------------------------------------- contraction tuner
+    // Shape class: ceil(log2) of M, N and K (capacities), products, Pi (combine) or frame form, dtype.
+    static int lg(int v) {
+        int l = 0;
+        while ((1 << l) < v && l < 30) ++l;
+        return l;
+    }
+    static unsigned long long shape_key(int M, int N, int K, int nprod, int combine) {
+        return ((unsigned long long)lg(M) << 24) | ((unsigned long long)lg(N) << 16) | ((unsigned long long)lg(K) << 8) |
+               ((unsigned long long)nprod << 2) | ((unsigned long long)combine << 1) | (is_cplx ? 1ull : 0ull);
+    }
+    int units_per_sm(int M, int N, int K, int nprod, int combine) const {
+        if (ctx->gemm_units.empty()) return aci::kGemmUnitsPerSm;
+        auto it = ctx->gemm_units.find(shape_key(M, N, K, nprod, combine));
+        return it == ctx->gemm_units.end() ? aci::kGemmUnitsPerSm : it->second;
+    }
+    // Time every candidate granularity on each untuned shape class of this call (operands of the
+    // class's size, zero-filled: the FP64 pipe's timing does not depend on the values) and keep the
+    // fastest. Runs on the context stream before the sweeps.
+    void tune_contractions() {
+        static const int cand[] = {1, 2, 4, 8};
+        std::vector<GemmShape> todo;
+        std::map<unsigned long long, int> seen;
+        for (const GemmShape& g : gemm_shapes) {
+            const unsigned long long k = shape_key(g.M, g.N, g.K, g.nprod, g.combine);
+            if (ctx->gemm_units.count(k) || seen.count(k)) continue;
+            seen[k] = 1;
+            todo.push_back(g);
+        }
+        if (todo.empty()) return;
+        size_t ea = 1, eb = 1, ec = 1;
+        for (const GemmShape& g : todo) {
+            ea = std::max(ea, (size_t)g.M * g.K);
+            eb = std::max(eb, (size_t)g.K * g.N);
+            ec = std::max(ec, (size_t)g.M * g.N);
+        }
+        const size_t bytes = sizeof(T) * (ea + eb + 2 * ec) + 1024;
+        char* buf = static_cast<char*>(dev_alloc(ctx, bytes));
+        cudaEvent_t e0 = get_event(), e1 = get_event();
+        try {
+            ck(ctx, cudaMemsetAsync(buf, 0, bytes, st), "tuner operands");
+            T* A = reinterpret_cast<T*>(buf);
+            T* B = A + ea;
+            T* C = B + eb;
+            for (const GemmShape& sh : todo) {
+                aci::GemmArgs<T> g = gemm_base();
+                g.combine = sh.combine;
+                g.nprod = sh.nprod;
+                for (int n = 0; n < sh.nprod; ++n) {
+                    g.A[n] = A;
+                    g.B[n] = B;
+                    g.C[n] = sh.combine ? C : C + (n & 1) * ec;
+                    g.M[n] = dimc(sh.M);
+                    g.N[n] = dimc(sh.N);
+                    g.K[n] = dimc(sh.K);
+                    g.lda[n] = dimc(sh.K);
+                    g.ldb[n] = dimc(sh.N);
+                }
+                g.chi = chi;
+                g.part = gpart;
+                g.tile_count = gcount;
+                g.num_sms = ctx->num_sms;
+                int best = aci::kGemmUnitsPerSm;
+                float best_ms = 1e30f;
+                for (int c : cand) {
+                    g.target_units = aci::gemm_target_units(ctx->num_sms, c);
+                    aci::launch_gemm<T>(g, sh.M, sh.N, st);  // warm-up
+                    ck(ctx, cudaEventRecord(e0, st), "event");
+                    for (int r = 0; r < 3; ++r) aci::launch_gemm<T>(g, sh.M, sh.N, st);
+                    ck(ctx, cudaEventRecord(e1, st), "event");
+                    ck(ctx, cudaEventSynchronize(e1), "tuner");
+                    ctx->launches += 4;
+                    float ms = 0.f;
+                    ck(ctx, cudaEventElapsedTime(&ms, e0, e1), "tuner");
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = c;
+                    }
+                }
+                ctx->gemm_units[shape_key(sh.M, sh.N, sh.K, sh.nprod, sh.combine)] = best;
+            }
+        } catch (Fail&) {
+            ctx->evfree.push_back(e0);
+            ctx->evfree.push_back(e1);
+            dev_free(ctx, buf);
+            throw;
+        }
+        ctx->evfree.push_back(e0);
+        ctx->evfree.push_back(e1);
+        dev_free(ctx, buf);
+    }
+
     // ---------------------------------------------------------------- launches
     // Kmax: the largest K of the products (a host-known input or initial-guess rank).
     void gemm(aci::GemmArgs<T>& g, int Mmax, int Nmax, int Kmax, const char* what, int cls) {
@@ -495,7 +597,7 @@ struct Run {
         g.flops = flops_of(cls);
         g.part = gpart;
         g.tile_count = gcount;
-        g.target_units = aci::gemm_target_units(ctx->num_sms);
+        g.target_units = aci::gemm_target_units(ctx->num_sms, units_per_sm(Mmax, Nmax, Kmax, g.nprod, g.combine));
         g.num_sms = ctx->num_sms;
         cudaEvent_t e = pre(cls);
         if (digits) {
@@ -946,6 +1048,7 @@ struct Run {
         ck(ctx, cudaMemsetAsync(ll, 0, ll_words * sizeof(unsigned long long), st), "clear exchange");
         prrlu_launches = 0;
         ck(ctx, cudaMemsetAsync(gcount, 0, gcount_n * sizeof(int), st), "clear counters");
+        if (autotune && !digits) tune_contractions();
         if (hist_on) {  // -1 marks updates that never ran
             ck(ctx, cudaMemsetAsync(hist_rank, 0xFF, sizeof(int) * hist_slots * nb, st), "history");
             ck(ctx, cudaMemsetAsync(hist_rows, 0xFF, sizeof(int) * (size_t)hist_slots * nb * chimax, st), "history");
@@ -1431,6 +1534,7 @@ aci_status run_typed(aci_ctx* ctx, int N, const aci_tt* const* ins, aci_op op, d
     R.seed = o.seed;
     R.hist_on = stats && stats->hist_rank && stats->hist_rows && stats->hist_cols && a->L > 1;
     R.hist_slots = 1 + 2 * o.max_sweeps;
+    R.autotune = o.autotune ? 1 : 0;
     R.op = make_op<T>(op);
     R.init = o.init;
     R.host_in = a->memory == ACI_MEM_HOST;

@@ -225,13 +225,14 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
 
 }  // namespace
 
-int gemm_target_units(int num_sms) { return 4 * num_sms; }
+int gemm_target_units(int num_sms, int per_sm) { return per_sm * num_sms; }
 
 size_t gemm_part_elems(int Mmax, int Nmax, int nprod, int combine, int num_sms) {
     const size_t tiles = (size_t)((Mmax + BM - 1) / BM) * ((Nmax + BN - 1) / BN);
     const size_t per_kc = combine ? tiles * nprod : tiles * nprod;
-    // units < target + per_kc (k chunks are rounded up from target / per_kc)
-    return (size_t)(gemm_target_units(num_sms) + per_kc) * BM * BN;
+    // units < target + per_kc (k chunks are rounded up from target / per_kc); sized for the
+    // largest target the split-K tuner may choose
+    return (size_t)(gemm_target_units(num_sms, kGemmMaxUnitsPerSm) + per_kc) * BM * BN;
 }
 
 size_t gemm_tile_counters(int Mmax, int Nmax, int nprod) {

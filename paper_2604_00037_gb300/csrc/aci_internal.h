@@ -28,7 +28,11 @@ template <class T> struct GemmArgs {
 };
 
 template <class T> void launch_gemm(const GemmArgs<T>& g, int Mmax, int Nmax, cudaStream_t st);
-int gemm_target_units(int num_sms);
+// Split-K granularity: about per_sm work units per SM (default kGemmUnitsPerSm; the contraction
+// tuner of aci_opts.autotune chooses among 1, 2, 4 and 8 per shape class).
+constexpr int kGemmUnitsPerSm = 4;
+constexpr int kGemmMaxUnitsPerSm = 8;
+int gemm_target_units(int num_sms, int per_sm = kGemmUnitsPerSm);
 size_t gemm_part_elems(int Mmax, int Nmax, int nprod, int combine, int num_sms);
 size_t gemm_tile_counters(int Mmax, int Nmax, int nprod);
 

@@ -159,10 +159,10 @@ __global__ void __launch_bounds__(256) gather_kernel(GatherArgs<T> a) {
     const int sld = dimv(j.sld, a.chi), dld = dimv(j.dld, a.chi);
     const int cblk = j.cblk.mul ? dimv(j.cblk, a.chi) : 0;
     const int cstride = j.cblk.mul ? dimv(j.cstride, a.chi) : 0;
-    const long long n = (long long)rows * cols;
+    const int n = rows * cols;  // < 2^31: the host rejects larger blocks
     unsigned long long mk = 0;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(e / cols), c = (int)(e - (long long)r * cols);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int r = e / cols, c = e - r * cols;  // 32-bit division (a 64-bit one costs several times more)
         const T v = j.src[(size_t)gather_row(j.ridx, j.rblk, r) * sld + gather_col(j.cidx, cblk, cstride, c)];
         j.dst[(size_t)r * dld + c] = v;
         const unsigned long long k = key_of(v);

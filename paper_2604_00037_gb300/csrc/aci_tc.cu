@@ -35,6 +35,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include <cstdlib>
+
 #include "aci_internal.h"
 
 namespace aci {
@@ -383,13 +385,20 @@ __global__ void __launch_bounds__(kGemmThreads, 2) tc_gemm_kernel(TcArgs<T> a) {
                 const uint64_t db = dB0 + stoff + ((uint64_t)(ks * slabB) >> 4);
                 for (int i = 0; i < S; ++i) {
                     const uint64_t da = dA0 + stoff + ((uint64_t)(ks * slabA + i * kSlabBytesA) >> 4);
-                    const uint32_t dt = tbase + (uint32_t)((s * S + i) * NT);
-                    const uint32_t idesc = idesc_bf16(kTileM, (S - i) * NT);
                     const uint32_t acc = (kc == 0 && ks == 0 && i == 0) ? 0u : 1u;  // i = 0 opens every order
-                    asm volatile(
-                        "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dt),
-                        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                    // B digits 0..S-1-i are stacked along N: (S - i) NT rows, cut into MMAs of N <= 256
+                    // (row r of the stack starts 16 r bytes into each K half of the slab)
+                    const int ntot = (S - i) * NT;
+                    for (int off = 0; off < ntot; off += 256) {
+                        const int nn = min(256, ntot - off);
+                        const uint32_t dt = tbase + (uint32_t)((s * S + i) * NT + off);
+                        const uint32_t idesc = idesc_bf16(kTileM, nn);
+                        const uint64_t dbo = db + (uint64_t)off;  // off rows x 16 bytes, in 16-byte units
+                        asm volatile(
+                            "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dt),
+                            "l"(da), "l"(dbo), "r"(idesc), "r"(acc));
+                    }
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -534,13 +543,28 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
+int tc_nt_override() {
+    static const int v = [] {
+        const char* e = std::getenv("ACI_TC_NT");
+        return e ? std::atoi(e) : 0;
+    }();
+    return v;
+}
+
 TcPlan tc_plan(int digits, bool cplx_values, int Mmax, int Nmax, int Kmax, int nprod, int combine) {
     TcPlan p;
     const int cmul = cplx_values ? 2 : 1;
     p.S = digits;
     p.nacc = combine ? nprod : 1;
-    // one MMA spans the S stacked B digits (N = S * NT <= 256); TMEM holds nacc * S * NT columns
+    // TMEM holds nacc * S * NT columns (<= 512). NT = 64 halves the re-reads of A's digit planes
+    // (every N tile reads them again), but above 4 digits its tensor memory no longer fits two
+    // CTAs per SM, and losing the overlap of one CTA's epilogue with the other's copies and MMAs
+    // costs more (2048 x 2048 x 256 complex: bf16x6 0.43 vs 0.40 ms, bf16x8 0.53 vs 0.46 ms).
+    // The S stacked B digits of an MMA are cut into MMAs of N <= 256. ACI_TC_NT overrides the
+    // width where tensor memory allows it (tuning only).
     p.NT = (digits <= 4) ? 64 : 32;
+    const int nt_env = tc_nt_override();
+    if ((nt_env == 32 || nt_env == 64) && (size_t)p.nacc * digits * nt_env <= 512) p.NT = nt_env;
     const long long K2 = (long long)cmul * std::max(Kmax, 1);
     p.bits = 7;
     while (p.bits > 2 && (long long)digits * K2 * ((1ll << p.bits) - 1) * ((1ll << p.bits) - 1) >= (1ll << 24))
@@ -568,8 +592,7 @@ TcPlan tc_plan(int digits, bool cplx_values, int Mmax, int Nmax, int Kmax, int n
         p.nst = (int)std::min<size_t>(8, (200 * 1024 - extra) / stage);
         p.smem = std::max<size_t>((size_t)p.nst * stage + extra, 120 * 1024);
     }
-    p.ok = digits >= kTcMinDigits && digits <= kTcMaxDigits && p.nst >= 1 && cols <= 512 && p.bits >= 3 &&
-           digits * p.NT <= 256;
+    p.ok = digits >= kTcMinDigits && digits <= kTcMaxDigits && p.nst >= 1 && cols <= 512 && p.bits >= 3;
     return p;
 }
 

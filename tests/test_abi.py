@@ -34,7 +34,7 @@ def test_struct_layouts_match_header():
     # sizes implied by include/aci.h on LP64
     assert ctypes.sizeof(binding.AciOp) == 8 + 64
     assert ctypes.sizeof(binding.AciTT) == 16 + 24
-    assert ctypes.sizeof(binding.AciOpts) == 16 + 8 + 8 + 8 + 8
+    assert ctypes.sizeof(binding.AciOpts) == 16 + 8 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(binding.AciStats) == 16 + 32 + 8 + 32 + 32 + 32 + 32 + 32 + 24
 
 

@@ -1,8 +1,8 @@
 """GPU checks of aci_elementwise_batch: independent products run concurrently on worker streams
 must give exactly what aci_elementwise_ex gives for each product alone (same kernels, same
 deterministic reductions), whatever the number of streams; a failing product reports its own
-status without disturbing the others. The whole method itself is pinned against the oracle by
-test_gpu_aci.py; one product of the batch is compared with the oracle here as well."""
+status without disturbing the others. Every product of a batch is also compared with the oracle
+(here, and for the batched workload's own pairs in test_gpu_dtypes.py)."""
 
 import numpy as np
 import pytest
@@ -64,15 +64,16 @@ def test_batch_equals_single_calls(ctx, streams, overlap):
         assert info["ranks"] == rinfo["ranks"] and info["iterations"] == rinfo["iterations"]
 
 
-def test_batch_product_matches_oracle_and_exact(ctx):
+def test_batch_products_match_oracle_and_exact(ctx):
     items = make_items(2, 4)
     res = ctx.elementwise_batch([dict(it, a=dev(it["a"]), b=dev(it["b"]) if it["b"] is not None else None)
                                  for it in items], streams=4)
-    it, (cores, info) = items[0], res[0]
-    ref = oracle.aci([it["a"], it["b"]], it["op"], it["tol"], it["max_rank"])
-    y = tt_full([c.cpu().numpy() for c in cores])
-    assert info["ranks"] == ref["ranks"]
-    assert np.abs(y - tt_full(ref["Y"])).max() <= 1e-12 * np.abs(tt_full(ref["Y"])).max()
+    for it, (cores, info) in zip(items, res):  # every product against the oracle
+        ins = [it["a"]] + ([it["b"]] if it["b"] is not None else [])
+        ref = oracle.aci(ins, it["op"], it["tol"], it["max_rank"])
+        y = tt_full([c.cpu().numpy() for c in cores])
+        assert info["ranks"] == ref["ranks"]
+        assert np.abs(y - tt_full(ref["Y"])).max() <= 1e-12 * np.abs(tt_full(ref["Y"])).max()
     for it, (cores, info) in zip(items, res):
         A = tt_full(it["a"])
         B = tt_full(it["b"]) if it["b"] is not None else None
@@ -111,3 +112,23 @@ def test_autotuned_concurrency_keeps_results(ctx):
         again = ctx.elementwise_batch(batch, streams=0)
         for (c1, i1), (c2, i2) in zip(first, again):
             assert same(c1, c2) and i1["ranks"] == i2["ranks"]
+
+
+def test_contraction_tuner_keeps_parity(ctx):
+    """aci_opts.autotune times the FP64 contractions' split-K granularity per shape class and keeps
+    the fastest in the context: only the summation order of the contractions changes, so the
+    products still meet the followed-parity bar against the oracle, alone and in a batch."""
+    from tests.parity import followed_parity
+    rng = np.random.default_rng(12)
+    a = tt_random_uniform(rng, 8, 2, 5, low=-1, high=1)
+    b = tt_random_uniform(rng, 8, 2, 4, low=-1, high=1)
+    for _ in range(2):  # the second call reuses the tuned table
+        followed_parity(ctx, [a, b], "mul", 1e-12, 64, gpu_kw=dict(autotune=True))
+    items = make_items(6, 5)
+    res = ctx.elementwise_batch([dict(it, a=dev(it["a"]), b=dev(it["b"]) if it["b"] is not None else None)
+                                 for it in items], streams=3, autotune=True)
+    for it, (cores, info) in zip(items, res):
+        ins = [it["a"]] + ([it["b"]] if it["b"] is not None else [])
+        ref = oracle.aci(ins, it["op"], it["tol"], it["max_rank"])
+        y = tt_full([c.cpu().numpy() for c in cores])
+        assert np.abs(y - tt_full(ref["Y"])).max() <= 1e-10 * np.abs(tt_full(ref["Y"])).max()
