@@ -54,11 +54,15 @@ def parse():
                     help="skip the per-sweep time and error curve")
     ap.add_argument("--no-cfg3", dest="cfg3", action="store_false", help="skip the fused d = 8 sub-object")
     ap.add_argument("--cfg3-chi", type=int, default=128)
+    ap.add_argument("--vs-chi", default="32,64,96", help="other input ranks of the workload timed beside the "
+                                                        "headline (empty: skip)")
     ap.add_argument("--batch-line", type=int, default=64,
                     help="pairs of the batched workload in the default line's batch object (0: skip it)")
     ap.add_argument("--mixed-digits", type=int, default=6, help="BF16 digit planes of the mixed run (0: skip it)")
     ap.add_argument("--precision", default="fp64", help="contractions of the headline run: fp64 or bf16xS")
     ap.add_argument("--pivot-mode", default="full", choices=["full", "rook"])
+    ap.add_argument("--autotune", type=int, default=0,
+                    help="1: the contraction split-K tuner (aci_opts.autotune) for the headline run")
     ap.add_argument("--overlap", default="auto", choices=["auto", "off", "on"],
                     help="schedule of the sweeps (aci_opts.sweep_overlap)")
     ap.add_argument("--kernel", default="", choices=["", "pi_block", "frame_gemm", "prrlu", "fp64peak"],
@@ -394,6 +398,7 @@ def config_dict(args, p):
             "L": 40, "d": 2, "chi": args.chi, "max_rank": p["max_rank"], "tol": p["tol"],
             "op": "a*b", "max_sweeps": args.max_sweeps,
             "contractions": args.precision, "pivot_search": args.pivot_mode, "sweep_overlap": args.overlap,
+            "contraction_tuner": bool(args.autotune),
             "l2": "flushed before every timed step (256 MB write, untimed)",
             "parallelism": f"replicas x{args.gpus}"}
 
@@ -643,6 +648,36 @@ def run_time_to_tol(ctx, A, B, a, b, p, args, stream):
                     "the max relative error against the exact product on seeded grid points"}
 
 
+def run_vs_chi(ctx, args, stream):
+    """Time per product of the same workload at other input ranks (the metric's time vs chi):
+    config 2 with chi from --vs-chi, max_rank 2 chi, tol 1e-10; median of 3 calls after one."""
+    import numpy as np
+    import torch
+    from synthetic.tt import tt_eval
+    rows = []
+    for chi in [int(c) for c in args.vs_chi.split(",") if c]:
+        p = workload(chi)
+        a, b = p["inputs"]
+        A, B = [torch.from_numpy(c).cuda() for c in a], [torch.from_numpy(c).cuda() for c in b]
+        call = lambda: ctx.elementwise(A, B, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps,
+                                       overlap=args.overlap, autotune=bool(args.autotune))
+        call()
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            y, info = call()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        pts = sample_points(np.random.default_rng(13), len(a), 2, 4000)
+        exact = tt_eval(a, pts) * tt_eval(b, pts)
+        rows.append({"chi": chi, "ms_per_product": statistics.median(ts), "iterations": info["iterations"],
+                     "max_rank": max(info["ranks"]), "max_eps_rel": info["max_eps"] / info["scale"],
+                     "rel_err_vs_exact": rel_err(tt_eval([c.cpu().numpy() for c in y], pts), exact)})
+    return rows
+
+
 def run_cfg3(ctx, args, stream, fp64_peak):
     """The fused d = 8 workload: |psi|^2 psi of a 3D complex field, 12 sites, chi = 128, tol 1e-8,
     max_rank chi, in FP64 and with BF16 digit-plane contractions (plain schedule at d = 8)."""
@@ -804,7 +839,7 @@ def main():
     def step(profile=False, history=False):
         return ctx.elementwise(A, B, "mul", p["tol"], p["max_rank"], max_sweeps=args.max_sweeps, profile=profile,
                                precision=args.precision, pivot_mode=args.pivot_mode, overlap=args.overlap,
-                               history=history)
+                               history=history, autotune=bool(args.autotune))
 
     for w in range(args.warmup):
         flush.fill_(w & 0xFF)
@@ -879,7 +914,7 @@ def main():
     bh = [torch.from_numpy(c).pin_memory().numpy() for c in b]
     h2d = sum(c.nbytes for c in ah) + sum(c.nbytes for c in bh)
     ekw = dict(max_sweeps=args.max_sweeps, out_memory="host", precision=args.precision, pivot_mode=args.pivot_mode,
-               overlap=args.overlap)
+               overlap=args.overlap, autotune=bool(args.autotune))
     ctx.elementwise(ah, bh, "mul", p["tol"], p["max_rank"], **ekw)
     e2e_t, d2h = [], 0
     for k in range(max(1, min(args.steps, 3))):
@@ -897,6 +932,7 @@ def main():
         e2e_value = world * len(e2e_t) / float(t.item())
 
     ttt = run_time_to_tol(ctx, A, B, a, b, p, args, stream) if args.time_to_tol and rank == 0 else None
+    vs_chi = run_vs_chi(ctx, args, stream) if args.vs_chi and rank == 0 else None
 
     # the same workload with the contractions on the tensor cores; errors on 20000 sampled points
     mixed = None
@@ -955,7 +991,7 @@ def main():
                 "result": {"iterations": last["iterations"], "converged": last["converged"],
                            "max_rank": max(last["ranks"]), "max_eps_rel": last["max_eps"] / last["scale"]},
                 "roofline": roofline, "fp64_peak_tflops": fp64_peak, "cpu_baseline": cpu,
-                "time_to_tol": ttt, "mixed": mixed, "cfg3": cfg3, "batch": batch_line,
+                "time_to_tol": ttt, "vs_chi": vs_chi, "mixed": mixed, "cfg3": cfg3, "batch": batch_line,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
                 "clocks": clk}
