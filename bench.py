@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="time this many independent pairs of the batched workload instead (aci_elementwise_batch)")
     ap.add_argument("--streams", type=int, default=0, help="batch: products in flight (0 = library default)")
+    ap.add_argument("--proposer-line", type=int, default=9,
+                    help="steps of the learned-proposal sequence (chi 128) in the default line's proposer object "
+                         "(0: skip it)")
     ap.add_argument("--proposer", action="store_true",
                     help="the learned-proposal sequence: train on steps 0-39, compare on 40-59")
     ap.add_argument("--seq-steps", type=int, default=60)
@@ -94,35 +97,37 @@ def _seq_pair(args):
     return sequence_config5_pair(t, chi)
 
 
-def run_proposer(args):
-    """The learned-proposal sequence (synthetic/fields.py, sequence_config5_pair): products f_t g_t,
-    tol 1e-8, max_rank 2 chi. Plain ACI runs steps 0 .. 2/3 of the sequence while recording the
-    (features, pivot-or-not) pairs of its left-to-right updates; the network is trained on them with
-    the library's kernels (Adam, weighted logistic loss); the remaining steps run with plain ACI and
-    with the learned restriction. Reports time per product, the error of both against the exact
-    product on 20000 sampled points, and the recall of plain ACI's pivots by the kept candidates."""
+def make_sequence(nsteps, chi):
+    """The learned-proposal sequence's inputs, generated in a spawned pool (before any GPU call)."""
     import multiprocessing as mp
-    import numpy as np
-    nsteps = args.seq_steps
-    ntrain = (2 * nsteps) // 3
     for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
     t0 = time.time()
-    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:  # before any GPU call
-        pairs = pool.map(_seq_pair, [(t, args.chi) for t in range(nsteps)])
-    gen_s = time.time() - t0
-    print(f"proposer: {nsteps} steps generated in {gen_s:.1f} s", file=sys.stderr, flush=True)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        pairs = pool.map(_seq_pair, [(t, chi) for t in range(nsteps)])
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.pop(v, None)
+    return pairs, time.time() - t0
+
+
+def proposer_measure(ctx, pairs, chi, keeps, max_sweeps, gen_s):
+    """Plain ACI runs the first two thirds of the sequence while recording the (features, pivot-or-
+    not) pairs of its left-to-right updates; the network is trained on them with the library's
+    kernels (Adam, weighted logistic loss); the remaining steps run with plain ACI and with the
+    learned restriction. Returns the time per product and the error against the exact product on
+    20000 sampled points of each, and the held-out AUC of the scores."""
+    import numpy as np
     import torch
-    from synthetic.weights import proposer_init
-    from paper_2604_00037_gb300.binding import Context
     from synthetic.tt import tt_eval
-    ctx = Context(0)
-    tol, max_rank = 1e-8, 2 * args.chi
+    from synthetic.weights import proposer_init
+    nsteps = len(pairs)
+    ntrain = (2 * nsteps) // 3
+    tol, max_rank = 1e-8, 2 * chi
     dev = lambda tt: [torch.from_numpy(c).cuda() for c in tt]
     read = ctx.record_proposer_data(4_000_000)
     for t in range(ntrain):
         a, b = pairs[t]
-        ctx.elementwise(dev(a), dev(b), "mul", tol, max_rank, max_sweeps=args.max_sweeps)
+        ctx.elementwise(dev(a), dev(b), "mul", tol, max_rank, max_sweeps=max_sweeps)
     X, y, nrec = read()
     pos = float(y.mean().item())
     P = torch.from_numpy(proposer_init(0, 7)).cuda()
@@ -136,7 +141,6 @@ def run_proposer(args):
     print(f"proposer: {X.shape[0]} records ({pos:.3f} positive), loss {loss:.4f}, {train_s:.1f} s", file=sys.stderr,
           flush=True)
     rng = np.random.default_rng(8)
-    keeps = [float(k) for k in str(args.keep).split(",")]
     modes = ["plain"] + ["proposed" if i == 0 else f"proposed@{k:g}" for i, k in enumerate(keeps)]
     rows = {m: [] for m in modes}
     for t in range(ntrain, nsteps):
@@ -151,7 +155,7 @@ def run_proposer(args):
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
-                ycores, info = ctx.elementwise(A, B, "mul", tol, max_rank, max_sweeps=args.max_sweeps,
+                ycores, info = ctx.elementwise(A, B, "mul", tol, max_rank, max_sweeps=max_sweeps,
                                                pivot_mode="full" if mode == "plain" else "proposed")
                 e1.record()
                 torch.cuda.synchronize()
@@ -163,10 +167,10 @@ def run_proposer(args):
                 "max_rel_err_vs_exact": float(np.max([r[1] for r in v])),
                 "mean_iterations": float(np.mean([r[2] for r in v])),
                 "max_rank": int(np.max([r[3] for r in v]))} for m, v in rows.items()}
-    # recall: of plain ACI's pivots in recorded held-out data, the share the proposer keeps
+    # held-out AUC of the scores on a recorded held-out product
     read = ctx.record_proposer_data(2_000_000)
     a, b = pairs[nsteps - 1]
-    ctx.elementwise(dev(a), dev(b), "mul", tol, max_rank, max_sweeps=args.max_sweeps)
+    ctx.elementwise(dev(a), dev(b), "mul", tol, max_rank, max_sweeps=max_sweeps)
     Xt, yt, _ = read()
     zt = ctx.mlp_forward(Xt, P, fp16=True).cpu().numpy()
     yt = yt.cpu().numpy()
@@ -174,13 +178,10 @@ def run_proposer(args):
     zp, zn = zt[yt > 0.5], zt[yt < 0.5]
     zp = zp[sub.permutation(len(zp))[:2000]]
     zn = zn[sub.permutation(len(zn))[:2000]]
-    line = {"metric": "learned pivot proposal: ACI time per product at equal error (held-out steps)",
-            "unit": "ms/product", "value": summ["proposed"]["ms_per_product"], "higher_is_better": False,
-            "dtype": "f64", "data": "synthetic", "n_gpus": 1,
-            "config": {"workload": f"{nsteps}-step sequence f_t g_t of 2D interleaved Fourier fields (L=40, d=2, "
-                                   f"chi={args.chi}), phases advancing by omega_k t; tol {tol:g}, max_rank {max_rank}; "
-                                   f"trained on steps 0-{ntrain - 1}, compared on {ntrain}-{nsteps - 1}",
-                       "keep": args.keep, "input_generation_s": gen_s},
+    return {"workload": f"{nsteps}-step sequence f_t g_t of 2D interleaved Fourier fields (L=40, d=2, chi={chi}), "
+                        f"phases advancing by omega_k t; tol {tol:g}, max_rank {max_rank}; trained on steps "
+                        f"0-{ntrain - 1}, compared on {ntrain}-{nsteps - 1}",
+            "keep": keeps, "input_generation_s": gen_s,
             "training": {"records": int(X.shape[0]), "positive_share": pos, "final_loss": loss,
                          "adam_steps": 400, "train_s": train_s},
             **{m: summ[m] for m in modes},
@@ -188,6 +189,19 @@ def run_proposer(args):
             **{f"speedup@{k:g}": summ["plain"]["ms_per_product"] / summ[m]["ms_per_product"]
                for k, m in zip(keeps, modes[1:])},
             "held_out_auc": float((zp[:, None] > zn[None, :]).mean()) if len(zp) and len(zn) else float("nan")}
+
+
+def run_proposer(args):
+    """The learned-proposal sequence alone (bench.py --proposer): see proposer_measure."""
+    pairs, gen_s = make_sequence(args.seq_steps, args.chi)
+    print(f"proposer: {len(pairs)} steps generated in {gen_s:.1f} s", file=sys.stderr, flush=True)
+    from paper_2604_00037_gb300.binding import Context
+    ctx = Context(0)
+    keeps = [float(k) for k in str(args.keep).split(",")]
+    res = proposer_measure(ctx, pairs, args.chi, keeps, args.max_sweeps, gen_s)
+    line = {"metric": "learned pivot proposal: ACI time per product at equal error (held-out steps)",
+            "unit": "ms/product", "value": res["proposed"]["ms_per_product"], "higher_is_better": False,
+            "dtype": "f64", "data": "synthetic", "n_gpus": 1, "config": {"workload": res["workload"]}, **res}
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -816,9 +830,11 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    batch = None
+    batch = seq = None
     if args.batch_line and rank == 0 and world == 1:
         batch = make_batch(args.batch_line)  # spawned pool: before any GPU call
+    if args.proposer_line and rank == 0 and world == 1:
+        seq = make_sequence(args.proposer_line, 128)  # spawned pool: before any GPU call
     import torch
     import torch.distributed as dist
 
@@ -976,6 +992,7 @@ def main():
 
     cfg3 = run_cfg3(ctx, args, stream, fp64_peak) if args.cfg3 and rank == 0 else None
     batch_line = run_batch_line(ctx, *batch, args, stream) if batch is not None else None
+    proposer_line = proposer_measure(ctx, seq[0], 128, [1.25], args.max_sweeps, seq[1]) if seq is not None else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -992,6 +1009,7 @@ def main():
                            "max_rank": max(last["ranks"]), "max_eps_rel": last["max_eps"] / last["scale"]},
                 "roofline": roofline, "fp64_peak_tflops": fp64_peak, "cpu_baseline": cpu,
                 "time_to_tol": ttt, "vs_chi": vs_chi, "mixed": mixed, "cfg3": cfg3, "batch": batch_line,
+                "proposer": proposer_line,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
                 "clocks": clk}

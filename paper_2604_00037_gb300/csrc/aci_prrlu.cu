@@ -174,23 +174,6 @@ __device__ __forceinline__ bool better(kbits_t k1, int l1, kbits_t k2, int l2) {
     return k1 > k2 || (k1 == k2 && l1 < l2);
 }
 
-// Can v's pivot key beat the running best (bkey, blin) of a scan in increasing position order?
-// A complex key re*re + im*im costs three FP64 operations (the scarcest issue slots on this GPU);
-// the exponents alone bound it: |re|, |im| < 2^(E - 1022) for biased exponents E, so the rounded
-// key is below 2^(2 max(E_re, E_im) - 2042), the double with biased exponent 2 max - 1019. When
-// that bound does not exceed the best key (non-negative doubles order like their bits) v loses,
-// ties included (a later position never wins one), and its key is not formed. Integer work only;
-// bounds outside the normal range, and the first entry of a scan, always take the exact key.
-__device__ __forceinline__ bool may_beat(double, kbits_t, int) { return true; }
-__device__ __forceinline__ bool may_beat(cplx v, kbits_t bkey, int blin) {
-    if (blin == INT_MAX) return true;
-    const int er = ((unsigned)__double2hiint(v.re) >> 20) & 0x7FF;
-    const int ei = ((unsigned)__double2hiint(v.im) >> 20) & 0x7FF;
-    const int eb = 2 * (er > ei ? er : ei) - 1019;
-    if (eb <= 0 || eb >= 2047) return true;
-    return ((kbits_t)eb << 52) > bkey;
-}
-
 // Block-wide (key, linear index) argmax; the result is returned to every thread.
 __device__ __forceinline__ void block_argmax(kbits_t& key, int& lin, kbits_t* skey, int* slin) {
 #pragma unroll
@@ -417,7 +400,6 @@ __global__ void __launch_bounds__(PT) prrlu_kernel(PrrluArgs<T> a) {
                 T* ptr = rowp + (size_t)cc * ldw;
                 const T v = s_fms(l, prow[cc], *ptr);
                 *ptr = v;
-                if (!may_beat(v, bkey, blin)) continue;
                 const kbits_t k = key_of(v);
                 if (better(k, rn + cc, bkey, blin)) { bkey = k; blin = rn + cc; }
             }
@@ -628,7 +610,6 @@ __global__ void __launch_bounds__(PT) prrlu_cluster_kernel(PrrluArgs<T> a) {
                 T* ptr = rowp + (size_t)cc * ldw;
                 const T v = s_fms(l, prow[cc], *ptr);
                 *ptr = v;
-                if (!may_beat(v, bkey, blin)) continue;
                 const kbits_t k = key_of(v);
                 if (better(k, rn + cc, bkey, blin)) { bkey = k; blin = rn + cc; }
             }
@@ -873,10 +854,8 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
                 if ((colmask >> cc) & 1u) {
                     const T x = s_fms(l[i], prow[cc], v[i][cc]);
                     v[i][cc] = x;
-                    if (may_beat(x, qk[cc & 3], ql[cc & 3])) {
-                        const kbits_t k = key_of(x);
-                        if (better(k, rn + cc, qk[cc & 3], ql[cc & 3])) { qk[cc & 3] = k; ql[cc & 3] = rn + cc; qv[cc & 3] = x; }
-                    }
+                    const kbits_t k = key_of(x);
+                    if (better(k, rn + cc, qk[cc & 3], ql[cc & 3])) { qk[cc & 3] = k; ql[cc & 3] = rn + cc; qv[cc & 3] = x; }
                 }
             }
         }
@@ -1061,10 +1040,8 @@ __global__ void __launch_bounds__(CT, 1) prrlu_cta_kernel(PrrluArgs<T> a) {
                 if ((colmask >> c) & 1u) {
                     const T x = s_fms(l[i], u[c], v[i][c]);
                     v[i][c] = x;
-                    if (may_beat(x, qk[c & 3], ql[c & 3])) {
-                        const kbits_t k = key_of(x);
-                        if (better(k, rn + c, qk[c & 3], ql[c & 3])) { qk[c & 3] = k; ql[c & 3] = rn + c; qv[c & 3] = x; }
-                    }
+                    const kbits_t k = key_of(x);
+                    if (better(k, rn + c, qk[c & 3], ql[c & 3])) { qk[c & 3] = k; ql[c & 3] = rn + c; qv[c & 3] = x; }
                 }
             }
         }
