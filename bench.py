@@ -61,8 +61,8 @@ def parse():
     ap.add_argument("--mixed-digits", type=int, default=6, help="BF16 digit planes of the mixed run (0: skip it)")
     ap.add_argument("--precision", default="fp64", help="contractions of the headline run: fp64 or bf16xS")
     ap.add_argument("--pivot-mode", default="full", choices=["full", "rook"])
-    ap.add_argument("--autotune", type=int, default=0,
-                    help="1: the contraction split-K tuner (aci_opts.autotune) for the headline run")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1 (default): the contraction tuner (aci_opts.autotune) for the headline run; 0: off")
     ap.add_argument("--overlap", default="auto", choices=["auto", "off", "on"],
                     help="schedule of the sweeps (aci_opts.sweep_overlap)")
     ap.add_argument("--kernel", default="", choices=["", "pi_block", "frame_gemm", "prrlu", "fp64peak"],

@@ -126,12 +126,15 @@ typedef struct {
                               products per 16 SMs (the width of one pivot-search cluster) on
                               successive calls, timing each, then keeps the fastest          */
     int32_t sweep_overlap; /* aci_overlap: schedule of the sweeps (results agree to rounding)    */
-    int32_t autotune;      /* 1: before its sweeps, a call times the FP64 contraction's split-K
-                              granularity (1, 2, 4 or 8 work units per SM) on every shape class it
-                              will launch (capacity buckets of M, N, K; products; Pi or frame form)
-                              that the context has not tuned yet, and keeps the fastest in the
-                              context for this and later calls; results are unchanged except for
-                              the summation order of the contractions. 0 (default): 4 per SM  */
+    int32_t autotune;      /* 1: before its sweeps, a call times its contractions' launch shape on
+                              every shape class it will launch (capacity buckets of M, N, K;
+                              products; Pi or frame form; precision) that the context has not tuned
+                              yet, and keeps the fastest in the context for this and later calls:
+                              for FP64 the split-K granularity (1, 2, 4 or 8 work units per SM), for
+                              digit planes the output tile width (128 x 32 or 128 x 64 where tensor
+                              memory allows). Results are unchanged except for the summation order
+                              of the FP64 contractions. 0 (default): 4 per SM; 64 wide up to 4
+                              digits, else 32                                                  */
     int32_t _pad2;
 } aci_opts;
 

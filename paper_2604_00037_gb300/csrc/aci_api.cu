@@ -75,8 +75,10 @@ struct aci_ctx {
     // diagnostic wait limits (aci_set_wait_limits); 0 = the defaults
     long long exchange_polls = 0;
     long long pipeline_polls = 0;
-    // split-K granularity per contraction shape class, from the tuner of aci_opts.autotune
+    // split-K granularity (FP64) and output tile width (digit planes) per contraction shape class,
+    // from the tuner of aci_opts.autotune
     std::map<unsigned long long, int> gemm_units;
+    std::map<unsigned long long, int> tc_widths;
 };
 
 namespace {
@@ -448,6 +450,10 @@ struct Run {
             gemm_shapes.push_back({Mm, Nm, rmax, nprod, combine});
             if (digits) {  // K of every contraction is an input rank or an initial-guess rank
                 const aci::TcPlan p = aci::tc_plan(digits, is_cplx, Mm, Nm, rmax, nprod, combine);
+                for (int nt : {32, 64}) {  // the tuner may choose either width: room for both
+                    const aci::TcPlan q = aci::tc_plan(digits, is_cplx, Mm, Nm, rmax, nprod, combine, nt);
+                    if (q.ok) tc_bytes = std::max(tc_bytes, aci::tc_scratch_bytes(q));
+                }
                 if (!p.ok) {
                     if (optional) {
                         overlap = 0;
@@ -509,6 +515,11 @@ struct Run {
         return ((unsigned long long)lg(M) << 24) | ((unsigned long long)lg(N) << 16) | ((unsigned long long)lg(K) << 8) |
                ((unsigned long long)nprod << 2) | ((unsigned long long)combine << 1) | (is_cplx ? 1ull : 0ull);
     }
+    int tc_width(int M, int N, int K, int nprod, int combine) const {
+        if (ctx->tc_widths.empty()) return 0;
+        auto it = ctx->tc_widths.find(shape_key(M, N, K, nprod, combine) ^ ((unsigned long long)digits << 40));
+        return it == ctx->tc_widths.end() ? 0 : it->second;
+    }
     int units_per_sm(int M, int N, int K, int nprod, int combine) const {
         if (ctx->gemm_units.empty()) return aci::kGemmUnitsPerSm;
         auto it = ctx->gemm_units.find(shape_key(M, N, K, nprod, combine));
@@ -519,11 +530,13 @@ struct Run {
     // fastest. Runs on the context stream before the sweeps.
     void tune_contractions() {
         static const int cand[] = {1, 2, 4, 8};
+        static const int widths[] = {32, 64};
         std::vector<GemmShape> todo;
         std::map<unsigned long long, int> seen;
+        const unsigned long long dkey = (unsigned long long)digits << 40;
         for (const GemmShape& g : gemm_shapes) {
-            const unsigned long long k = shape_key(g.M, g.N, g.K, g.nprod, g.combine);
-            if (ctx->gemm_units.count(k) || seen.count(k)) continue;
+            const unsigned long long k = shape_key(g.M, g.N, g.K, g.nprod, g.combine) ^ dkey;
+            if ((digits ? ctx->tc_widths.count(k) : ctx->gemm_units.count(k)) || seen.count(k)) continue;
             seen[k] = 1;
             todo.push_back(g);
         }
@@ -560,13 +573,28 @@ struct Run {
                 g.part = gpart;
                 g.tile_count = gcount;
                 g.num_sms = ctx->num_sms;
-                int best = aci::kGemmUnitsPerSm;
+                int best = digits ? 0 : aci::kGemmUnitsPerSm;
                 float best_ms = 1e30f;
-                for (int c : cand) {
-                    g.target_units = aci::gemm_target_units(ctx->num_sms, c);
-                    aci::launch_gemm<T>(g, sh.M, sh.N, st);  // warm-up
+                const int ncand = digits ? 2 : 4;
+                for (int ci = 0; ci < ncand; ++ci) {
+                    const int c = digits ? widths[ci] : cand[ci];
+                    if (digits) {
+                        const aci::TcPlan q = aci::tc_plan(digits, is_cplx, sh.M, sh.N, sh.K, sh.nprod, sh.combine, c);
+                        if (!q.ok || q.NT != c || aci::tc_scratch_bytes(q) > tc_bytes) continue;
+                    } else {
+                        g.target_units = aci::gemm_target_units(ctx->num_sms, c);
+                    }
+                    auto launch = [&]() {
+                        if (digits)
+                            ck(ctx, aci::launch_gemm_tc<T>(g, sh.M, sh.N, sh.K, digits, tcbuf, tc_bytes, err, nullptr, st,
+                                                           ctx->pipeline_polls, c),
+                               "tuner");
+                        else
+                            aci::launch_gemm<T>(g, sh.M, sh.N, st);
+                    };
+                    launch();  // warm-up
                     ck(ctx, cudaEventRecord(e0, st), "event");
-                    for (int r = 0; r < 3; ++r) aci::launch_gemm<T>(g, sh.M, sh.N, st);
+                    for (int r = 0; r < 3; ++r) launch();
                     ck(ctx, cudaEventRecord(e1, st), "event");
                     ck(ctx, cudaEventSynchronize(e1), "tuner");
                     ctx->launches += 4;
@@ -577,7 +605,8 @@ struct Run {
                         best = c;
                     }
                 }
-                ctx->gemm_units[shape_key(sh.M, sh.N, sh.K, sh.nprod, sh.combine)] = best;
+                if (digits) ctx->tc_widths[shape_key(sh.M, sh.N, sh.K, sh.nprod, sh.combine) ^ dkey] = best;
+                else ctx->gemm_units[shape_key(sh.M, sh.N, sh.K, sh.nprod, sh.combine)] = best;
             }
         } catch (Fail&) {
             ctx->evfree.push_back(e0);
@@ -602,7 +631,8 @@ struct Run {
         cudaEvent_t e = pre(cls);
         if (digits) {
             ck(ctx, aci::launch_gemm_tc<T>(g, Mmax, Nmax, Kmax, digits, tcbuf, tc_bytes, err,
-                                           prof ? kflops + 4 + cls : nullptr, st, ctx->pipeline_polls),
+                                           prof ? kflops + 4 + cls : nullptr, st, ctx->pipeline_polls,
+                                           tc_width(Mmax, Nmax, Kmax, g.nprod, g.combine)),
                what);
             ctx->launches++;  // digit split + tensor-core contraction
             kcount[cls]++;
@@ -1048,7 +1078,7 @@ struct Run {
         ck(ctx, cudaMemsetAsync(ll, 0, ll_words * sizeof(unsigned long long), st), "clear exchange");
         prrlu_launches = 0;
         ck(ctx, cudaMemsetAsync(gcount, 0, gcount_n * sizeof(int), st), "clear counters");
-        if (autotune && !digits) tune_contractions();
+        if (autotune) tune_contractions();
         if (hist_on) {  // -1 marks updates that never ran
             ck(ctx, cudaMemsetAsync(hist_rank, 0xFF, sizeof(int) * hist_slots * nb, st), "history");
             ck(ctx, cudaMemsetAsync(hist_rows, 0xFF, sizeof(int) * (size_t)hist_slots * nb * chimax, st), "history");

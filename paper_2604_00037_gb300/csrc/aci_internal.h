@@ -71,12 +71,13 @@ struct TcPlan {
     bool ok;
 };
 // Kmax: largest K of the launch's products (complex counts once; the plan doubles it).
-TcPlan tc_plan(int digits, bool cplx_values, int Mmax, int Nmax, int Kmax, int nprod, int combine);
+// nt_pref: the output tile width to use (32 or 64) where tensor memory allows it; 0 = the default rule.
+TcPlan tc_plan(int digits, bool cplx_values, int Mmax, int Nmax, int Kmax, int nprod, int combine, int nt_pref = 0);
 size_t tc_scratch_bytes(const TcPlan& p);
 template <class T>
 cudaError_t launch_gemm_tc(const GemmArgs<T>& g, int Mmax, int Nmax, int Kmax, int digits, void* scratch,
                            size_t scratch_bytes, int* err, double* tc_flops, cudaStream_t st,
-                           long long wait_polls = 0);
+                           long long wait_polls = 0, int nt_pref = 0);
 
 template <class T> struct PrrluArgs {
     const T* Min;       // m x n row-major input, not modified

@@ -551,7 +551,7 @@ int tc_nt_override() {
     return v;
 }
 
-TcPlan tc_plan(int digits, bool cplx_values, int Mmax, int Nmax, int Kmax, int nprod, int combine) {
+TcPlan tc_plan(int digits, bool cplx_values, int Mmax, int Nmax, int Kmax, int nprod, int combine, int nt_pref) {
     TcPlan p;
     const int cmul = cplx_values ? 2 : 1;
     p.S = digits;
@@ -563,8 +563,8 @@ TcPlan tc_plan(int digits, bool cplx_values, int Mmax, int Nmax, int Kmax, int n
     // The S stacked B digits of an MMA are cut into MMAs of N <= 256. ACI_TC_NT overrides the
     // width where tensor memory allows it (tuning only).
     p.NT = (digits <= 4) ? 64 : 32;
-    const int nt_env = tc_nt_override();
-    if ((nt_env == 32 || nt_env == 64) && (size_t)p.nacc * digits * nt_env <= 512) p.NT = nt_env;
+    const int nt_want = nt_pref ? nt_pref : tc_nt_override();  // the contraction tuner's choice, else the override
+    if ((nt_want == 32 || nt_want == 64) && (size_t)p.nacc * digits * nt_want <= 512) p.NT = nt_want;
     const long long K2 = (long long)cmul * std::max(Kmax, 1);
     p.bits = 7;
     while (p.bits > 2 && (long long)digits * K2 * ((1ll << p.bits) - 1) * ((1ll << p.bits) - 1) >= (1ll << 24))
@@ -600,10 +600,11 @@ size_t tc_scratch_bytes(const TcPlan& p) { return p.bytesA + p.bytesB + p.bytesE
 
 template <class T>
 cudaError_t launch_gemm_tc(const GemmArgs<T>& g, int Mmax, int Nmax, int Kmax, int digits, void* scratch,
-                           size_t scratch_bytes, int* err, double* tc_flops, cudaStream_t st, long long wait_polls) {
+                           size_t scratch_bytes, int* err, double* tc_flops, cudaStream_t st, long long wait_polls,
+                           int nt_pref) {
     if (Mmax <= 0 || Nmax <= 0) return cudaSuccess;
     const bool cv = sizeof(T) == sizeof(cplx);
-    const TcPlan p = tc_plan(digits, cv, Mmax, Nmax, Kmax, g.nprod, g.combine);
+    const TcPlan p = tc_plan(digits, cv, Mmax, Nmax, Kmax, g.nprod, g.combine, nt_pref);
     if (!p.ok || tc_scratch_bytes(p) > scratch_bytes) return cudaErrorInvalidValue;
     TcArgs<T> a;
     for (int q = 0; q < 2; ++q) {
@@ -657,8 +658,8 @@ cudaError_t launch_gemm_tc(const GemmArgs<T>& g, int Mmax, int Nmax, int Kmax, i
 }
 
 template cudaError_t launch_gemm_tc<double>(const GemmArgs<double>&, int, int, int, int, void*, size_t, int*, double*,
-                                            cudaStream_t, long long);
+                                            cudaStream_t, long long, int);
 template cudaError_t launch_gemm_tc<cplx>(const GemmArgs<cplx>&, int, int, int, int, void*, size_t, int*, double*,
-                                          cudaStream_t, long long);
+                                          cudaStream_t, long long, int);
 
 }  // namespace aci

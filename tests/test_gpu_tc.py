@@ -260,3 +260,19 @@ def test_config2_mixed_precision_sampled_error(ctx):
     yv, fv = tt_eval(y, pts), tt_eval(a, pts) * tt_eval(b, pts)
     assert np.abs(yv - fv).max() / np.abs(fv).max() <= 1e-8
     assert max(info["ranks"]) <= p["max_rank"]
+
+
+@pytest.mark.parametrize("S", [4, 6])
+def test_tuned_tile_width_keeps_accuracy(ctx, S):
+    """aci_opts.autotune chooses the digit-plane contraction's output tile width (128 x 32 or 128 x 64)
+    per shape class by timing both: the digits and their sums are the same either way, so the
+    product meets the same bar against the oracle."""
+    p = config_inputs(1)
+    a, b = p["inputs"]
+    ref = tt_full(oracle.aci([a, b], "mul", p["tol"], p["max_rank"])["Y"])
+    for _ in range(2):  # the second call reuses the tuned table
+        got, info = ctx.elementwise([dev(c) for c in a], [dev(c) for c in b], "mul", p["tol"], p["max_rank"],
+                                    precision=f"bf16x{S}", autotune=True)
+        y = [c.cpu().numpy() for c in got]
+        bound = 1e-8 if S >= 5 else 1e-6
+        assert np.abs(tt_full(y) - ref).max() <= bound * np.abs(ref).max()
