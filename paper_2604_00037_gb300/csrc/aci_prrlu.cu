@@ -13,15 +13,16 @@
 // each), so small blocks run in one CTA with no grid-wide synchronisation at all. CTA g owns a
 // contiguous block of columns, kept column-major in shared memory when the worst case fits
 // (else in an L2-resident global copy). The pivot steps are strictly sequential; each one
-// costs exactly one exchange between CTAs, made of self-validating 8-byte words: the low 32
-// bits carry data, the high 32 bits the step's tag. Every CTA writes its best candidate
-// (key, position, value) and that candidate's column as such words, then polls the G records
-// of the step; because every 8-byte word is written and read atomically and carries its own
-// tag, no fence, acquire or release is needed, and a word from an older step can never be
-// mistaken for a current one. Records and columns alternate between two buffers by step
-// parity: a CTA can only overwrite a buffer after every other CTA has published its next
-// record, which each does only after it has read the buffer. The caller clears the exchange
-// area once per sequence of launches and gives each launch a distinct tag base.
+// costs one exchange of candidates between CTAs, made of self-validating 8-byte words: the low
+// 32 bits carry data, the high 32 bits the step's tag. Every CTA writes its best candidate (key,
+// position, value) as such words, then polls the G records of the step; because every 8-byte word
+// is written and read atomically and carries its own tag, no fence, acquire or release is needed,
+// and a word from an older step can never be mistaken for a current one. After the decision the
+// CTA that owns the winning column publishes it the same way and the others read it. Records and
+// columns alternate between two buffers by step parity: a CTA can only overwrite a buffer after
+// every other CTA has published its next record, which each does only after it has read the
+// buffer. The caller clears the exchange area once per sequence of launches and gives each launch
+// a distinct tag base.
 // The Schur update of step p is fused with the local argmax of step p+1.
 #include <algorithm>
 #include <climits>
@@ -136,7 +137,18 @@ __device__ __forceinline__ double fast_recip(double d) {
     return fma(r, e, r);
 }
 __device__ __forceinline__ double recip_of(double d) { return fast_recip(d); }
-__device__ __forceinline__ cplx recip_of(cplx d) { return s_div(s_one(cplx()), d); }
+// 1/d for a complex pivot: conj(d) / |d|^2 with the real reciprocal above, when both parts are
+// within 2^(+-480) (so |d|^2 neither overflows nor loses precision); Smith's division (two FP64
+// divisions, ~1100 cycles on the step's critical path) otherwise. Each part is within a few units
+// in the last place of the exact reciprocal's.
+__device__ __forceinline__ cplx recip_of(cplx d) {
+    const unsigned er = ((unsigned)__double2hiint(d.re) >> 20) & 0x7FFu;
+    const unsigned ei = ((unsigned)__double2hiint(d.im) >> 20) & 0x7FFu;
+    const unsigned e = er > ei ? er : ei;
+    if (e < 1023u - 480u || e > 1023u + 480u) return s_div(s_one(cplx()), d);
+    const double r = fast_recip(fma(d.re, d.re, d.im * d.im));
+    return mkc(d.re * r, -d.im * r);
+}
 
 // The stop test of Algorithm 2 and the multiplier scale for the step's winner. For real values
 // |pivot| <= tau and pivot == 0 are decided on the key bits (exact: keys are non-negative
@@ -291,11 +303,7 @@ __global__ void __launch_bounds__(PT) prrlu_kernel(PrrluArgs<T> a) {
         } else {
             // publish: candidate column and record, as tagged words (no fence needed)
             unsigned long long* myrec = recs + ((size_t)buf * G + g) * kRecWords;
-            unsigned long long* mycol = cols + ((size_t)buf * G + g) * (size_t)mmax * WPV;
-            if (blin != INT_MAX) {
-                const T* colp = Wb + (size_t)(blin % n - c0) * ldw;
-                for (int r = tid; r < m; r += PT) put_val(mycol + (size_t)r * WPV, colp[r], tag);
-            }
+            // the column itself is published by the winner's owner, after the decision
             if (tid == 0) {
                 st_word(myrec, (unsigned int)(bkey >> 32), tag);
                 st_word(myrec + 1, (unsigned int)bkey, tag);
@@ -345,10 +353,16 @@ __global__ void __launch_bounds__(PT) prrlu_kernel(PrrluArgs<T> a) {
         }
         // Multipliers S[r, cj] / pivot from the winning column; pivot row of the own columns.
         // Row ri and column cj become used here; the loops below never read those flags for them.
-        if (Ge == 1) {
+        // Only the winning column's owner publishes it (tagged words, read by the other CTAs): one
+        // column per step crosses L2 instead of every CTA's candidate column.
+        if (Ge == 1 || g == gw) {
             const T* colp = Wb + (size_t)(cj - c0) * ldw;
-            for (int r = tid; r < m; r += PT)
-                lcol[r] = (rowused[r] || r == ri || zpiv) ? s_zero(T()) : s_mul(colp[r], inv);
+            unsigned long long* oc = cols + ((size_t)buf * G + g) * (size_t)mmax * WPV;
+            for (int r = tid; r < m; r += PT) {
+                const T v = colp[r];
+                if (Ge > 1) put_val(oc + (size_t)r * WPV, v, tag);
+                lcol[r] = (rowused[r] || r == ri || zpiv) ? s_zero(T()) : s_mul(v, inv);
+            }
         } else {
             const unsigned long long* wc = cols + ((size_t)buf * G + gw) * (size_t)mmax * WPV;
             for (int r = tid; r < m; r += PT) {
