@@ -25,8 +25,10 @@ __device__ __forceinline__ cplx s_one(cplx) { return mkc(1.0, 0.0); }
 __device__ __forceinline__ double s_add(double a, double b) { return a + b; }
 __device__ __forceinline__ cplx s_add(cplx a, cplx b) { return mkc(a.re + b.re, a.im + b.im); }
 __device__ __forceinline__ double s_mul(double a, double b) { return a * b; }
+// The complex product with its fused multiply-adds written out: left to the compiler, which of
+// the two products it fuses may differ from kernel to kernel, and so would the rounding.
 __device__ __forceinline__ cplx s_mul(cplx a, cplx b) {
-    return mkc(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+    return mkc(fma(a.re, b.re, -__dmul_rn(a.im, b.im)), fma(a.re, b.im, __dmul_rn(a.im, b.re)));
 }
 // acc + a * b
 __device__ __forceinline__ double s_fma(double a, double b, double acc) { return fma(a, b, acc); }
@@ -51,12 +53,13 @@ __device__ __forceinline__ cplx s_conj(cplx a) { return mkc(a.re, -a.im); }
 __device__ __forceinline__ double s_div(double a, double b) { return a / b; }
 __device__ __forceinline__ cplx s_div(cplx a, cplx b) {
     // Smith's algorithm (R. L. Smith, CACM 1962) to avoid overflow in |b|^2.
+    // (fused multiply-adds written out, as in s_mul)
     if (fabs(b.re) >= fabs(b.im)) {
-        double r = b.im / b.re, den = b.re + b.im * r;
-        return mkc((a.re + a.im * r) / den, (a.im - a.re * r) / den);
+        const double r = b.im / b.re, den = fma(b.im, r, b.re);
+        return mkc(fma(a.im, r, a.re) / den, fma(-a.re, r, a.im) / den);
     } else {
-        double r = b.re / b.im, den = b.re * r + b.im;
-        return mkc((a.re * r + a.im) / den, (a.im * r - a.re) / den);
+        const double r = b.re / b.im, den = fma(b.re, r, b.im);
+        return mkc(fma(a.re, r, a.im) / den, fma(a.im, r, -a.re) / den);
     }
 }
 __device__ __forceinline__ bool s_iszero(double a) { return a == 0.0; }

@@ -108,6 +108,7 @@ template <class T> struct PrrluArgs {
     long long spin_limit;  // > 0: exchange waits give up after that many polls (diagnostics); 0: kSpinLimit
     // filled by launch_prrlu
     int epc, wcap_elems, wcap_cols;
+    int grid_c;         // column groups of the 2D register variant (its cluster is grid_r x grid_c CTAs)
     // Live-shape split between the single-CTA variant and the variant chosen for the capacity:
     // a block with m <= small_m, n <= small_n and m n <= small_elems is factorised by the single-CTA
     // kernel and any other by the capacity's variant; each kernel returns at once when the block

@@ -121,16 +121,18 @@ template <class T> struct __align__(16) Decision {
     T piv;
 };
 
-// 1/d for a real pivot: an FP32 reciprocal as the seed, then two Newton-Raphson steps
-// r <- r + r (1 - d r) in FP64 (each step squares the relative error: 2^-23 -> 2^-46 -> below
-// one ulp). On this GPU a dependent FP64 operation takes ~63 cycles and a correctly rounded
-// division ~570, and the reciprocal sits on the critical path of every pivot step. Outside the
-// FP32 exponent range the division is used instead.
+// 1/d for a real pivot: the hardware's approximate FP64 reciprocal (PTX rcp.approx.ftz.f64) as
+// the seed, then two Newton-Raphson steps r <- r + r (1 - d r) in FP64; each step squares the
+// relative error, so a seed good to about 20 bits ends below one ulp (the GPU tests check every
+// result against 1/x to two ulp). On this GPU a dependent FP64 operation takes ~63 cycles and a
+// correctly rounded division ~570, and the reciprocal sits on the critical path of every pivot
+// step. Outside 2^(+-99) (no subnormal seed) the division is used instead.
 __device__ __forceinline__ double fast_recip(double d) {
     // range test on the biased exponent (integer work): 2^-99 <= |d| < 2^100
     const unsigned ex = ((unsigned)__double2hiint(d) >> 20) & 0x7FFu;
     if (ex < 1023u - 99u || ex >= 1023u + 100u) return 1.0 / d;
-    double r = (double)(1.0f / (float)d);
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
     double e = fma(-d, r, 1.0);
     r = fma(r, e, r);
     e = fma(-d, r, 1.0);
@@ -656,15 +658,6 @@ __global__ void __launch_bounds__(PT) prrlu_cluster_kernel(PrrluArgs<T> a) {
 constexpr int RT = 512;
 constexpr int RWARP = RT / 32;
 
-__device__ __forceinline__ double shfl_x(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
-__device__ __forceinline__ cplx shfl_x(cplx v, int off) {
-    return mkc(__shfl_xor_sync(0xffffffffu, v.re, off), __shfl_xor_sync(0xffffffffu, v.im, off));
-}
-__device__ __forceinline__ double shfl_0(double v) { return __shfl_sync(0xffffffffu, v, 0); }
-__device__ __forceinline__ cplx shfl_0(cplx v) {
-    return mkc(__shfl_sync(0xffffffffu, v.re, 0), __shfl_sync(0xffffffffu, v.im, 0));
-}
-
 __device__ __forceinline__ double shfl_from(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ cplx shfl_from(cplx v, int src) {
     return mkc(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
@@ -893,6 +886,395 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
         if (a.out_chi_idx >= 0) const_cast<int*>(a.chi)[a.out_chi_idx] = p;
     }
     cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// ---------------------------------------------------------------- 2D register-resident cluster variant
+// The C = Cr x Cc CTAs of the cluster tile the block as a Cr x Cc grid: CTA (rg, cg) holds rows
+// [R0, R1) and columns [C0, C1) in registers, lane l the rows R0 + l + 32 i, warp w the columns
+// C0 + w CC + j. The candidate exchange is the 1D variant's (every CTA writes its candidate into
+// every CTA's slots; one cluster barrier). After the decision only the CTAs holding the pivot
+// column send its entries, each to the Cc CTAs of its row group, and only those holding the pivot
+// row send theirs, each to the Cr CTAs of its column group, with st.async stores that complete on
+// the receiving CTA's mbarrier. With a 1D column split every CTA reads the whole pivot column
+// from its owner, whose shared-memory port (about 32 bytes per clock) then serves C m values per
+// step, ~C m / 4 cycles (measured: ~1900 cycles of a ~7700-cycle step at m = 480, C = 16); here
+// no SM sends more than Cc (R1 - R0) + Cr (C1 - C0) values. Thread 0 forms the pivot reciprocal
+// while the values are in flight and arrives on the mbarrier with the expected byte count. The
+// multipliers l = S[r, j] / pivot of the CTA's rows and its entries of U's row are formed once
+// (one thread per row or column, not once per warp: a warp-wide FP64 multiply holds an SM
+// sub-partition's FP64 unit ~64 cycles) and shared through one block barrier. The arithmetic of
+// every entry is that of the other variants, so all of them choose the same pivots.
+constexpr int DT = 512;
+constexpr int DWARP = DT / 32;
+
+__device__ __forceinline__ uint32_t smem_u32addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// The shared::cluster address of the same offset in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t peer_addr(uint32_t a, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_async_val(uint32_t addr, double v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(addr),
+                 "l"(__double_as_longlong(v)), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async_val(uint32_t addr, cplx v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b64 [%0], {%1, %2}, [%3];" ::"r"(addr),
+                 "l"(__double_as_longlong(v.re)), "l"(__double_as_longlong(v.im)), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr unsigned long long kC2dWaitNs = 1000000000ull;  // 1 s per wait
+
+__device__ __forceinline__ void mb_init(uint32_t bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mb_arrive_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+// Has the phase of parity `parity` completed? Acquire at cluster scope: the st.async values that
+// other CTAs sent are visible once it has.
+__device__ __forceinline__ bool mb_done_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, "
+        "p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// The same test without the hardware's bounded suspend of try_wait (returns at once).
+__device__ __forceinline__ bool mb_test_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, "
+        "p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait (bounded) for the phase of parity `parity`: `polls` > 0 non-blocking tests at most (a
+// diagnostic limit, so that a short limit really runs out), else kC2dWaitNs of polling. False
+// when the wait ran out.
+__device__ __forceinline__ bool mb_wait_bounded(uint32_t bar, uint32_t parity, long long polls) {
+    if (polls > 0) {
+        for (long long it = 0; it < polls; ++it)
+            if (mb_test_cluster(bar, parity)) return true;
+        return false;
+    }
+    if (mb_done_cluster(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mb_done_cluster(bar, parity)) return true;
+        if ((it & 63u) == 0 && globaltimer_ns() - t0 > kC2dWaitNs) return false;
+    }
+}
+
+// Shared-memory bytes of the 2D variant (rcol, lsm [32 RR] | rrow [DWARP CC] | cand [2][C] |
+// warp maxima [DWARP] | 1 / pivot | mbarrier | used rows [32 RR] | used columns [DWARP CC]).
+template <class T>
+__host__ __device__ constexpr size_t c2d_vals_bytes(int rr, int cc) {
+    return (sizeof(T) * (2 * 32 * (size_t)rr + (size_t)DWARP * cc) + 15) & ~(size_t)15;
+}
+template <class T>
+size_t c2d_bytes(int rr, int cc, int C) {
+    size_t b = c2d_vals_bytes<T>(rr, cc);
+    b += sizeof(Cand<T>) * (2 * (size_t)C + DWARP);
+    b += ((sizeof(T) + 15) & ~(size_t)15) + 16;
+    b += 32 * (size_t)rr + (size_t)DWARP * cc;
+    return (b + 15) & ~(size_t)15;
+}
+
+template <class T, int RR, int CC>
+__global__ void __launch_bounds__(DT, 1) prrlu_c2d_kernel(PrrluArgs<T> a) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int g = (int)cl.block_rank();
+    const int Cc = a.grid_c, Cr = C / Cc;
+    const int rg = g / Cc, cgr = g - rg * Cc;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m = dimv(a.m, a.chi), n = dimv(a.n, a.chi);
+    if (small_block(a, m, n)) return;  // every CTA of the cluster returns before any exchange
+    const int R0 = (int)(((long long)m * rg) / Cr), R1 = (int)(((long long)m * (rg + 1)) / Cr);
+    const int C0 = (int)(((long long)n * cgr) / Cc), C1 = (int)(((long long)n * (cgr + 1)) / Cc);
+    const int nr = R1 - R0, nc = C1 - C0;  // <= 32 RR and <= DWARP CC (the host sizes RR, CC for the capacity)
+
+    T* rcol = reinterpret_cast<T*>(smem_raw);  // received entries of the pivot column, local rows
+    T* lsm = rcol + 32 * RR;                    // multipliers of the local rows
+    T* rrow = lsm + 32 * RR;                    // received entries of the pivot row, local columns
+    Cand<T>* cand = reinterpret_cast<Cand<T>*>(smem_raw + c2d_vals_bytes<T>(RR, CC));
+    Cand<T>* wmx = cand + 2 * C;
+    T* sinv = reinterpret_cast<T*>(wmx + DWARP);
+    unsigned long long* mbar = align16<unsigned long long>(sinv + 1);
+    int* sfail = reinterpret_cast<int*>(mbar + 1);  // a wait of this CTA ran out
+    unsigned char* used_r = reinterpret_cast<unsigned char*>(mbar + 2);
+    unsigned char* used_c = used_r + 32 * RR;
+    const uint32_t bar = smem_u32addr(mbar);
+    const uint32_t rcol_a = smem_u32addr(rcol), rrow_a = smem_u32addr(rrow);
+    if (tid == 0) {
+        *sfail = 0;
+        mb_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int t = tid; t < 32 * RR; t += DT) {
+        used_r[t] = (unsigned char)(t >= nr);
+        lsm[t] = s_zero(T());  // rows past the CTA's own keep a zero multiplier
+    }
+    for (int t = tid; t < DWARP * CC; t += DT) used_c[t] = (unsigned char)(t >= nc);
+
+    const int cw = C0 + warp * CC;  // this warp's first column
+    unsigned int colmask = 0;
+#pragma unroll
+    for (int j = 0; j < CC; ++j)
+        if (cw + j < C1) colmask |= 1u << j;
+    // Rows that are not (or no longer) live hold zeros, get a zero multiplier, and take positions
+    // past every live one (rb), so the branch-free update leaves them at zero and they can only
+    // win the argmax when no live entry is left, which the stop test excludes (p < min(m, n)).
+    T v[RR][CC];
+    bool live[RR];
+    int rb[RR];  // position of the row's entry in column cw (+ j for column cw + j)
+    kbits_t bkey = 0;
+    int blin = INT_MAX;
+    T bval = s_zero(T());
+#pragma unroll
+    for (int i = 0; i < RR; ++i) {
+        const int r = R0 + lane + 32 * i;
+        live[i] = r < R1;
+        rb[i] = live[i] ? cpos(r, cw) : INT_MAX - CC;
+#pragma unroll
+        for (int j = 0; j < CC; ++j) {
+            T x = s_zero(T());
+            if (live[i] && ((colmask >> j) & 1u)) {
+                x = a.Min[(size_t)r * n + cw + j];
+                const kbits_t k = key_of(x);
+                const int pos = cpos(r, cw + j);
+                if (better(k, pos, bkey, blin)) { bkey = k; blin = pos; bval = x; }
+            }
+            v[i][j] = x;
+        }
+    }
+
+    const int kmax = min(min(m, n), a.chimax);
+    const double S = a.rel ? __longlong_as_double((long long)*a.smax) : 0.0;
+    const double tau = a.rel ? a.tol * S : a.tol;
+    const uint32_t rbytes = (uint32_t)(((size_t)nr + (size_t)nc) * sizeof(T));
+
+    int p = 0;
+    double eps = 0.0;
+    for (;;) {
+        const int par = p & 1;
+        // (1) the CTA's candidate, and its copy into every CTA's slots
+        int dummy = 0;
+        warp_best(bkey, blin, bval, dummy);
+        if (lane == 0) {
+            wmx[warp].key = bkey;
+            wmx[warp].lin = blin;
+            wmx[warp].val = bval;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            kbits_t ck = 0;
+            int cl_ = INT_MAX, cs = 0;
+            T cv = s_zero(T());
+            if (lane < DWARP) { ck = wmx[lane].key; cl_ = wmx[lane].lin; cv = wmx[lane].val; }
+            warp_best(ck, cl_, cv, cs);
+            Cand<T> mine;
+            mine.key = ck;
+            mine.lin = cl_;
+            mine.pad = *sfail;
+            mine.val = cv;
+            for (int t = lane; t < C; t += 32) *cl.map_shared_rank(cand + par * C + g, t) = mine;
+        }
+        cl.sync();
+        // (2) the winner among the C candidates and the step's decision, taken by every warp alike
+        kbits_t wk = 0;
+        int wl = INT_MAX, gw = 0, bad = 0;
+        T pv = s_zero(T());
+        if (lane < C) {
+            const Cand<T>& c = cand[par * C + lane];
+            wk = c.key;
+            wl = c.lin;
+            pv = c.val;
+            gw = lane;
+            bad = c.pad;
+        }
+        if (__any_sync(0xffffffffu, bad)) {  // a CTA's previous wait ran out: every CTA stops here
+            if (g == 0 && tid == 0) atomicOr(a.err, DEVERR_TIMEOUT);
+            break;
+        }
+        warp_best(wk, wl, pv, gw);
+        Decision<T> dl;
+        decide(&dl, wk, wl, pv, p, kmax, tau, false);
+        if (dl.code) {
+            if (dl.code == 2 && g == 0 && tid == 0) atomicOr(a.err, DEVERR_NUMERIC);
+            eps = dl.eps;
+            break;
+        }
+        const int zpiv = dl.zpiv;
+        const int ri = cpos_row(wl), cj = cpos_col(wl);
+        if (g == 0 && tid == 0) {
+            a.piv_rows[p] = ri;
+            a.piv_cols[p] = cj;
+            a.D[p] = pv;
+        }
+        // (3) the pivot column's entries of rows [R0, R1) to the Cc CTAs of this row group (sent by
+        //     the warp holding the column), the pivot row's entries of columns [C0, C1) to the Cr
+        //     CTAs of this column group (every warp sends its CC of them)
+        if (cj >= C0 && cj < C1 && warp == (cj - C0) / CC) {
+            const int jc = cj - cw;
+#pragma unroll
+            for (int i = 0; i < RR; ++i) {
+                const int rl = lane + 32 * i;
+                if (rl < nr) {
+                    const T x = select_reg<T, CC>(v[i], jc);
+                    const uint32_t la = rcol_a + (uint32_t)(rl * sizeof(T));
+                    for (int q = 0; q < Cc; ++q) {
+                        const int dst = rg * Cc + q;
+                        st_async_val(peer_addr(la, dst), x, peer_addr(bar, dst));
+                    }
+                }
+            }
+        }
+        if (ri >= R0 && ri < R1) {
+            const int rl = ri - R0, li = rl & 31, ii = rl >> 5;
+            T rv[CC];
+#pragma unroll
+            for (int j = 0; j < CC; ++j) {
+                T x = v[0][j];
+#pragma unroll
+                for (int i = 1; i < RR; ++i)
+                    if (i == ii) x = v[i][j];
+                rv[j] = shfl_from(x, li);
+            }
+            for (int q = lane; q < CC * Cr; q += 32) {
+                const int j = q % CC, d = q / CC;
+                const int cloc = warp * CC + j;  // local column
+                if (cloc < nc) {
+                    const T x = select_reg<T, CC>(rv, j);
+                    const int dst = d * Cc + cgr;
+                    st_async_val(peer_addr(rrow_a + (uint32_t)(cloc * sizeof(T)), dst), x, peer_addr(bar, dst));
+                }
+            }
+        }
+        // (4) thread 0 forms 1 / pivot while the entries are in flight, then arrives with the byte
+        //     count this CTA receives. Only the warps that form multipliers or U entries from the
+        //     received entries wait for the phase (bounded); the block barrier below orders what
+        //     they saw before the other warps' reads.
+        if (tid == 0) {
+            *sinv = zpiv ? s_zero(T()) : recip_of(pv);
+            mb_arrive_expect(bar, rbytes);
+        }
+        const int uw0 = (DT - DWARP * CC) >> 5;  // first warp of the U entries
+        const bool lrole = warp < ((nr + 31) >> 5);
+        const bool urole = warp >= uw0 && warp < uw0 + ((nc + 31) >> 5);
+        if (lrole || urole) {
+            if (!mb_wait_bounded(bar, (uint32_t)par, a.spin_limit)) *sfail = 1;  // every CTA stops at the next exchange
+        }
+        const T inv = *sinv;
+        // (5) multipliers of the local rows and this CTA's entries of row p of U, one thread each
+        if (tid < nr) {
+            const int r = R0 + tid;
+            T l = s_zero(T());
+            if (r == ri) used_r[tid] = 1;
+            else if (!used_r[tid]) l = s_mul(rcol[tid], inv);
+            lsm[tid] = l;
+            if (a.L && cgr == 0) a.L[(size_t)p * a.Lld + r] = (r == ri) ? s_one(T()) : l;
+        }
+        if (tid >= DT - DWARP * CC && tid - (DT - DWARP * CC) < nc) {
+            const int t = tid - (DT - DWARP * CC), c = C0 + t;
+            T u = s_zero(T());
+            if (c == cj) {
+                u = s_one(T());
+                used_c[t] = 1;
+            } else if (!used_c[t] && !zpiv) {
+                u = s_mul(rrow[t], inv);
+            }
+            if (a.U && rg == 0) a.U[(size_t)p * a.Uld + c] = u;
+        }
+#pragma unroll
+        for (int i = 0; i < RR; ++i)
+            if (R0 + lane + 32 * i == ri) {
+                live[i] = false;
+                rb[i] = INT_MAX - CC;
+#pragma unroll
+                for (int j = 0; j < CC; ++j) v[i][j] = s_zero(T());
+            }
+        if (cj >= cw && cj < cw + CC) colmask &= ~(1u << (cj - cw));
+        __syncthreads();
+        // (6) Schur-complement update in registers, fused with the next local argmax: one chain per
+        //     row slot; along a row the positions grow with j, so a later entry wins only with a
+        //     strictly larger key, and the chain keeps the key and the column index alone. The
+        //     first live column is the chain's start, which makes a row of zeros report its lowest
+        //     live position.
+        T u[CC];
+#pragma unroll
+        for (int j = 0; j < CC; ++j) u[j] = rrow[warp * CC + j];
+        const int jfirst = __ffs(colmask) - 1;
+        kbits_t qk[RR];
+        int qj[RR];
+#pragma unroll
+        for (int i = 0; i < RR; ++i) {
+            qk[i] = 0;
+            qj[i] = jfirst;
+            if (!__any_sync(0xffffffffu, live[i])) continue;  // warp-uniform: no live row in this slot
+            const T li = lsm[lane + 32 * i];
+#pragma unroll
+            for (int j = 0; j < CC; ++j) {
+                if ((colmask >> j) & 1u) {
+                    const T x = s_fms(li, u[j], v[i][j]);
+                    v[i][j] = x;
+                    const kbits_t k = key_of(x);
+                    if (k > qk[i]) { qk[i] = k; qj[i] = j; }
+                }
+            }
+        }
+        bkey = 0;
+        blin = INT_MAX;
+        bval = s_zero(T());
+        if (colmask) {
+#pragma unroll
+            for (int i = 0; i < RR; ++i) {
+                const int pos = rb[i] + qj[i];
+                if (better(qk[i], pos, bkey, blin)) {
+                    bkey = qk[i];
+                    blin = pos;
+                    bval = select_reg<T, CC>(v[i], qj[i]);
+                }
+            }
+        }
+        ++p;
+    }
+    // A wait of step p - 1 ran out (the loop then stopped at step p, before sending anything):
+    // let the entries of that step still in flight to this CTA land before it leaves (bounded).
+    if (*sfail && p > 0) {
+        const unsigned long long t0 = globaltimer_ns();
+        for (unsigned it = 0; !mb_done_cluster(bar, (uint32_t)((p - 1) & 1)); ++it)
+            if ((it & 63u) == 0 && globaltimer_ns() - t0 > kC2dWaitNs) break;
+    }
+    if (g == 0 && tid == 0) {
+        if (a.flops) {
+            const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
+            double f = 0.0;
+            for (int q = 0; q < p; ++q) f += (double)(m - q - 1) * (double)(n - q - 1);
+            atomicAdd(a.flops, per * f);
+        }
+        *a.eps_out = eps;
+        if (a.k_out) *a.k_out = p;
+        if (a.out_chi_idx >= 0) const_cast<int*>(a.chi)[a.out_chi_idx] = p;
+    }
+    cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
 // ---------------------------------------------------------------- single-CTA variant
@@ -1154,11 +1536,6 @@ __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_re
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -1178,8 +1555,9 @@ __device__ __forceinline__ void rk_get_val(const unsigned long long* p, cplx& v)
 // with the best one's value, returned to every thread. A record is one 128-byte line: the data
 // words, then a ready word holding the tag, stored with release semantics after a fence that
 // orders the CTA's earlier global writes (residual buffers, L, U; the barrier before it collects
-// them from every thread). Warp 0 polls only the ready words (acquire loads), reads each record
-// once, and the closing barrier passes the acquired view to the whole CTA. false: a wait ran out.
+// them from every thread). Each thread polls the ready words of its records (relaxed loads, then
+// one acquire fence) and reads each record once; the closing barrier passes the acquired view to
+// the whole CTA. false: a wait ran out.
 template <class T>
 __device__ bool rk_exchange(unsigned long long* area, unsigned int tag, RkCand<T> mine, RkCand<T>& out,
                             RkCand<T>* s, int* sok) {
@@ -1585,6 +1963,84 @@ int prrlu_small_elems() {
     return v;
 }
 
+// The 2D variant for RR rows per lane and CC columns per warp (values per thread: RR CC <= 32
+// real, <= 16 complex); nullptr where there is no instantiation.
+template <class T>
+void (*c2d_kernel(int rr, int cc))(PrrluArgs<T>) {
+    if (rr == 1) {
+        if (cc == 2) return prrlu_c2d_kernel<T, 1, 2>;
+        if (cc == 4) return prrlu_c2d_kernel<T, 1, 4>;
+        if (cc == 8) return prrlu_c2d_kernel<T, 1, 8>;
+    } else if (rr == 2) {
+        if (cc == 2) return prrlu_c2d_kernel<T, 2, 2>;
+        if (cc == 4) return prrlu_c2d_kernel<T, 2, 4>;
+        if constexpr (sizeof(T) == sizeof(double))  // complex: 16 values spill
+            if (cc == 8) return prrlu_c2d_kernel<T, 2, 8>;
+    } else if (rr == 4) {
+        if (cc == 2) return prrlu_c2d_kernel<T, 4, 2>;
+        if (cc == 4) return prrlu_c2d_kernel<T, 4, 4>;
+        if constexpr (sizeof(T) == sizeof(double))
+            if (cc == 8) return prrlu_c2d_kernel<T, 4, 8>;
+    }
+    return nullptr;
+}
+
+// ACI_PRRLU_2D: 1 (default) the 2D variant for the launch shapes it is faster on, 2 wherever it
+// fits, 0 nowhere; ACI_PRRLU_GRIDC=q fixes its column-group count (launch-shape tuning only: the
+// pivots are the same).
+int prrlu_2d_mode() {
+    static const int v = [] {
+        const char* e = std::getenv("ACI_PRRLU_2D");
+        return e ? std::atoi(e) : 1;
+    }();
+    return v;
+}
+int prrlu_gridc_override() {
+    static const int v = [] {
+        const char* e = std::getenv("ACI_PRRLU_GRIDC");
+        return e ? std::max(0, std::atoi(e)) : 0;
+    }();
+    return v;
+}
+
+static int pow2_at_least(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// The 2D variant's grid for the capacity: Cr x Cc <= cmax CTAs and the per-thread tile (RR, CC)
+// minimising a per-step cost in cycles (the FP64 update of a full tile: 4 warps per sub-partition,
+// ~64 cycles per warp-wide multiply-add, x4 for complex; the busiest sender's bytes at ~32 bytes
+// per clock; ~60 cycles of cluster barrier per CTA). Returns false when no instantiation fits.
+template <class T>
+bool c2d_plan(int mmax, int nmax, int cmax, int* Cr_out, int* Cc_out, int* rr_out, int* cc_out) {
+    const bool cp = sizeof(T) == sizeof(cplx);
+    double best = 0.0;
+    bool found = false;
+    for (int Cr = 1; Cr <= cmax; Cr <<= 1)
+        for (int Cc = 1; Cr * Cc <= cmax; Cc <<= 1) {
+            if (prrlu_gridc_override() > 0 && Cc != prrlu_gridc_override()) continue;
+            if (prrlu_cluster_override() > 0 && Cr * Cc != prrlu_cluster_override()) continue;
+            const int rows = (mmax + Cr - 1) / Cr, cols = (nmax + Cc - 1) / Cc;
+            const int rr = pow2_at_least((rows + 31) / 32);
+            const int cc = std::max(2, pow2_at_least((cols + DWARP - 1) / DWARP));
+            if (!c2d_kernel<T>(rr, cc)) continue;
+            const double upd = 256.0 * rr * cc * (cp ? 4.0 : 1.0);
+            const double xch = ((double)Cc * rows + (double)Cr * cols) * sizeof(T) / 32.0;
+            const double cost = upd + xch + 60.0 * Cr * Cc;
+            if (!found || cost < best) {
+                found = true;
+                best = cost;
+                *Cr_out = Cr;
+                *Cc_out = Cc;
+                *rr_out = rr;
+                *cc_out = cc;
+            }
+        }
+    return found;
+}
+
 // The single-CTA kernel for capacities up to 32 ROWS x 8 W (ROWS rows per lane, W columns per warp).
 template <class T>
 void (*cta_kernel(int rows, int w))(PrrluArgs<T>) {
@@ -1685,6 +2141,38 @@ cudaError_t launch_prrlu(const PrrluArgs<T>& a_in, int G, cudaStream_t st) {
         C = std::max(C, std::min(cmax, (a.nmax + kCregColsPerCta - 1) / kCregColsPerCta));
         C = std::max(1, std::min(C, a.nmax));
         if (prrlu_cluster_override() > 0) C = std::max(1, std::min(std::min(prrlu_cluster_override(), cmax), a.nmax));
+        const int wneed = (a.nmax + C - 1) / C;
+        const int rows = (a.mmax + RT - 1) / RT;
+        // The 2D variant where it measured faster than the 1D register variant (per launch, GB300):
+        // complex blocks, real blocks of more than 512 rows, and real blocks whose 1D split leaves at
+        // most 8 columns per CTA; the 1D variant keeps real blocks of up to 512 rows and 9-32 columns
+        // per CTA (at 480 x 480 it took 1.37 ms against 1.52). ACI_PRRLU_2D = 2 takes the 2D variant
+        // wherever it fits, 0 nowhere.
+        const bool prefer2d = cp || rows > 1 || wneed <= 8;
+        int Cr = 0, Cc = 0, rr = 0, cc = 0;
+        if ((prrlu_2d_mode() == 2 || (prrlu_2d_mode() == 1 && prefer2d)) &&
+            c2d_plan<T>(a.mmax, a.nmax, cmax, &Cr, &Cc, &rr, &cc)) {
+            void (*fn)(PrrluArgs<T>) = c2d_kernel<T>(rr, cc);
+            a.epc = 0;
+            a.wcap_cols = cc;
+            a.wcap_elems = 0;
+            a.grid_c = Cc;
+            cudaError_t e = kernel_attrs((const void*)fn);
+            if (e != cudaSuccess) return e;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(Cr * Cc);
+            cfg.blockDim = dim3(DT);
+            cfg.dynamicSmemBytes = c2d_bytes<T>(rr, cc, Cr * Cc);
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = Cr * Cc;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            return cudaLaunchKernelEx(&cfg, fn, a);
+        }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(C);
         cfg.stream = st;
@@ -1695,8 +2183,6 @@ cudaError_t launch_prrlu(const PrrluArgs<T>& a_in, int G, cudaStream_t st) {
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        const int wneed = (a.nmax + C - 1) / C;
-        const int rows = (a.mmax + RT - 1) / RT;
         void (*reg)(PrrluArgs<T>) = nullptr;
         int wmax = 0;
         // register budget: at most 32 values per thread (real) or 16 (complex)

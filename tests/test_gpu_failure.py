@@ -1,8 +1,8 @@
 """Failure detection without a GPU fault.
 
 Every device-side wait of the library is bounded: the pivot search's waits on other CTAs'
-exchange words (cooperative grid variant) and the tensor-core contraction's waits on its copy and
-multiply pipeline. aci_set_wait_limits shrinks those bounds to a few polls, so that an ordinary
+exchange words (cooperative grid variant) and on its pushed pivot row and column (2D register
+variant), and the tensor-core contraction's waits on its copy and multiply pipeline. aci_set_wait_limits shrinks those bounds to a few polls, so that an ordinary
 call runs them out: the kernels record a timeout, let their copies in flight finish, return, and
 the call reports ACI_E_TIMEOUT; restoring the defaults, the same context computes the right
 result again. An allocator hook that returns NULL makes a call fail with ACI_E_ALLOC and leave
@@ -52,6 +52,23 @@ def test_pivot_search_exchange_wait_runs_out(ctx):
     finally:
         ctx.set_wait_limits(0, 0)
     _compare_prrlu(ctx.prrlu(Md, tau, 300), oracle.ldu(M, tau, 300), M)  # the context is usable
+
+
+def test_pivot_search_push_wait_runs_out(ctx):
+    """1000 x 200 real: the 2D register variant (an 8 x 2 grid of CTAs), whose threads wait on the
+    mbarrier that the pushed pivot row and column entries complete; one non-blocking test per wait
+    runs out, and a run-out wait stops every CTA at the next exchange."""
+    from paper_2604_00037_gb300.binding import AciError
+    M = _graded(4, 1000, 200)
+    Md = torch.from_numpy(M).cuda()
+    tau = 1e-10 * np.abs(M).max()
+    ctx.set_wait_limits(exchange_polls=1)
+    try:
+        with pytest.raises(AciError, match="ACI_E_TIMEOUT"):
+            ctx.prrlu(Md, tau, 150)
+    finally:
+        ctx.set_wait_limits(0, 0)
+    _compare_prrlu(ctx.prrlu(Md, tau, 150), oracle.ldu(M, tau, 150), M)  # the context is usable
 
 
 def test_tensor_core_pipeline_wait_runs_out(ctx):

@@ -111,9 +111,10 @@ def _compare_prrlu(g, f, M):
 @pytest.mark.parametrize("shape,chimax,taurel", [
     ((1, 1), 4, 0.0), ((1, 9), 4, 0.0), ((13, 1), 4, 0.0), ((37, 53), 30, 0.0),
     ((37, 53), 100, 1e-3), ((128, 96), 64, 0.0), ((257, 300), 200, 1e-6), ((512, 512), 256, 1e-10),
-    # launch shapes of the other variants (capacity m x n decides): 128 x 300 complex and 600 x 400
-    # real take prrlu_cluster_kernel (cluster path, too wide for the register kernel); 700 x 700
-    # real and every larger complex block take the cooperative grid prrlu_kernel
+    # launch shapes of the other variants (capacity m x n decides): 128 x 96 and every complex
+    # block up to 2^16 entries take the 2D register kernel, 257 x 300 and 512 x 512 real the 1D one,
+    # 600 x 400 real prrlu_cluster_kernel (cluster path, too wide for either register kernel);
+    # 700 x 700 real and every larger complex block take the cooperative grid prrlu_kernel
     ((128, 300), 128, 1e-8), ((600, 400), 300, 1e-10), ((700, 700), 350, 1e-10)])
 def test_prrlu_matches_oracle(ctx, cplx, shape, chimax, taurel):
     m, n = shape
