@@ -109,6 +109,7 @@ template <class T> struct PrrluArgs {
     // filled by launch_prrlu
     int epc, wcap_elems, wcap_cols;
     int grid_c;         // column groups of the 2D register variant (its cluster is grid_r x grid_c CTAs)
+    int c2d_mbx;        // 1: the 2D variant exchanges candidates through mbarriers, not the cluster barrier
     // Live-shape split between the single-CTA variant and the variant chosen for the capacity:
     // a block with m <= small_m, n <= small_n and m n <= small_elems is factorised by the single-CTA
     // kernel and any other by the capacity's variant; each kernel returns at once when the block

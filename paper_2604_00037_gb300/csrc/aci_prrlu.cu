@@ -891,19 +891,22 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
 // ---------------------------------------------------------------- 2D register-resident cluster variant
 // The C = Cr x Cc CTAs of the cluster tile the block as a Cr x Cc grid: CTA (rg, cg) holds rows
 // [R0, R1) and columns [C0, C1) in registers, lane l the rows R0 + l + 32 i, warp w the columns
-// C0 + w CC + j. The candidate exchange is the 1D variant's (every CTA writes its candidate into
-// every CTA's slots; one cluster barrier). After the decision only the CTAs holding the pivot
-// column send its entries, each to the Cc CTAs of its row group, and only those holding the pivot
-// row send theirs, each to the Cr CTAs of its column group, with st.async stores that complete on
-// the receiving CTA's mbarrier. With a 1D column split every CTA reads the whole pivot column
-// from its owner, whose shared-memory port (about 32 bytes per clock) then serves C m values per
-// step, ~C m / 4 cycles (measured: ~1900 cycles of a ~7700-cycle step at m = 480, C = 16); here
-// no SM sends more than Cc (R1 - R0) + Cr (C1 - C0) values. Thread 0 forms the pivot reciprocal
-// while the values are in flight and arrives on the mbarrier with the expected byte count. The
-// multipliers l = S[r, j] / pivot of the CTA's rows and its entries of U's row are formed once
-// (one thread per row or column, not once per warp: a warp-wide FP64 multiply holds an SM
-// sub-partition's FP64 unit ~64 cycles) and shared through one block barrier. The arithmetic of
-// every entry is that of the other variants, so all of them choose the same pivots.
+// C0 + w CC + j. Every CTA sends its candidate into every CTA's slot with st.async stores that
+// complete on the receiver's candidate mbarrier of the step's parity (or, with ACI_PRRLU_MBX=0,
+// with plain DSMEM stores and the cluster barrier). After the decision only the CTAs holding the
+// pivot column send its entries, each to the Cc CTAs of its row group, and only those holding the
+// pivot row send theirs, each to the Cr CTAs of its column group, again as st.async stores on the
+// receiver's mbarrier: no SM sends more than Cc (R1 - R0) + Cr (C1 - C0) values per step, where the
+// 1D split has every CTA read the whole pivot column out of one SM (C m values). Thread 0 forms
+// the pivot reciprocal while the values are in flight and arrives on the mbarrier with the
+// expected byte count. The multipliers l = S[r, j] / pivot of the CTA's rows and its entries of
+// U's row are formed once (one thread per row or column, not once per warp: a warp-wide FP64
+// multiply holds an SM sub-partition's FP64 unit ~64 cycles) and shared through one block
+// barrier. Every wait is bounded; a run-out wait is reported with the next candidate and every
+// CTA stops there. The arithmetic of every entry is that of the other variants, so all of them
+// choose the same pivots (bit for bit). Measured against the 1D register variant it is faster on
+// complex blocks, on blocks of more than 512 rows and on narrow ones, slower on large square real
+// blocks (480 x 480: 1.56 vs 1.36 ms per call), where the FP64 update dominates both.
 constexpr int DT = 512;
 constexpr int DWARP = DT / 32;
 
@@ -930,6 +933,26 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 constexpr unsigned long long kC2dWaitNs = 1000000000ull;  // 1 s per wait
+
+// A candidate (32 bytes: key, position, flag, value) as two 16-byte st.async stores.
+template <class T>
+__device__ __forceinline__ void st_async_cand(uint32_t addr, const Cand<T>& c, uint32_t bar) {
+    const unsigned long long w1 = ((unsigned long long)(unsigned int)c.pad << 32) | (unsigned int)c.lin;
+    unsigned long long w2, w3;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        w2 = (unsigned long long)__double_as_longlong(reinterpret_cast<const double&>(c.val));
+        w3 = 0;
+    } else {
+        w2 = (unsigned long long)__double_as_longlong(reinterpret_cast<const double*>(&c.val)[0]);
+        w3 = (unsigned long long)__double_as_longlong(reinterpret_cast<const double*>(&c.val)[1]);
+    }
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b64 [%0], {%1, %2}, [%3];" ::"r"(addr),
+                 "l"(c.key), "l"(w1), "r"(bar)
+                 : "memory");
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b64 [%0], {%1, %2}, [%3];" ::"r"(addr + 16),
+                 "l"(w2), "l"(w3), "r"(bar)
+                 : "memory");
+}
 
 __device__ __forceinline__ void mb_init(uint32_t bar, int count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -981,7 +1004,8 @@ __device__ __forceinline__ bool mb_wait_bounded(uint32_t bar, uint32_t parity, l
 }
 
 // Shared-memory bytes of the 2D variant (rcol, lsm [32 RR] | rrow [DWARP CC] | cand [2][C] |
-// warp maxima [DWARP] | 1 / pivot | mbarrier | used rows [32 RR] | used columns [DWARP CC]).
+// warp maxima [DWARP] | 1 / pivot | mbarrier, flags | candidate mbarriers [2] | used rows [32 RR] |
+// used columns [DWARP CC]).
 template <class T>
 __host__ __device__ constexpr size_t c2d_vals_bytes(int rr, int cc) {
     return (sizeof(T) * (2 * 32 * (size_t)rr + (size_t)DWARP * cc) + 15) & ~(size_t)15;
@@ -990,7 +1014,7 @@ template <class T>
 size_t c2d_bytes(int rr, int cc, int C) {
     size_t b = c2d_vals_bytes<T>(rr, cc);
     b += sizeof(Cand<T>) * (2 * (size_t)C + DWARP);
-    b += ((sizeof(T) + 15) & ~(size_t)15) + 16;
+    b += ((sizeof(T) + 15) & ~(size_t)15) + 32;
     b += 32 * (size_t)rr + (size_t)DWARP * cc;
     return (b + 15) & ~(size_t)15;
 }
@@ -1017,15 +1041,21 @@ __global__ void __launch_bounds__(DT, 1) prrlu_c2d_kernel(PrrluArgs<T> a) {
     Cand<T>* cand = reinterpret_cast<Cand<T>*>(smem_raw + c2d_vals_bytes<T>(RR, CC));
     Cand<T>* wmx = cand + 2 * C;
     T* sinv = reinterpret_cast<T*>(wmx + DWARP);
-    unsigned long long* mbar = align16<unsigned long long>(sinv + 1);
-    int* sfail = reinterpret_cast<int*>(mbar + 1);  // a wait of this CTA ran out
-    unsigned char* used_r = reinterpret_cast<unsigned char*>(mbar + 2);
+    unsigned long long* mbar = align16<unsigned long long>(sinv + 1);  // pushed pivot row and column
+    int* sfail = reinterpret_cast<int*>(mbar + 1);      // a wait of this CTA ran out (reported)
+    int* shard = sfail + 1;                             // ... and its second, long wait too
+    unsigned long long* cbar = mbar + 2;                // [2] candidates by step parity (mbx)
+    unsigned char* used_r = reinterpret_cast<unsigned char*>(mbar + 4);
     unsigned char* used_c = used_r + 32 * RR;
-    const uint32_t bar = smem_u32addr(mbar);
+    const uint32_t bar = smem_u32addr(mbar), cbar_a = smem_u32addr(cbar);
     const uint32_t rcol_a = smem_u32addr(rcol), rrow_a = smem_u32addr(rrow);
+    const bool mbx = a.c2d_mbx != 0;
     if (tid == 0) {
         *sfail = 0;
+        *shard = 0;
         mb_init(bar, 1);
+        mb_init(cbar_a, 1);
+        mb_init(cbar_a + 8, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int t = tid; t < 32 * RR; t += DT) {
@@ -1070,11 +1100,14 @@ __global__ void __launch_bounds__(DT, 1) prrlu_c2d_kernel(PrrluArgs<T> a) {
     const double S = a.rel ? __longlong_as_double((long long)*a.smax) : 0.0;
     const double tau = a.rel ? a.tol * S : a.tol;
     const uint32_t rbytes = (uint32_t)(((size_t)nr + (size_t)nc) * sizeof(T));
+    if (mbx) cl.sync();  // every CTA's mbarriers are initialised before any CTA signals one
 
     int p = 0;
     double eps = 0.0;
     for (;;) {
         const int par = p & 1;
+        const uint32_t cb = cbar_a + 8u * (uint32_t)par;
+        if (mbx && tid == 0) mb_arrive_expect(cb, (uint32_t)(C * sizeof(Cand<T>)));
         // (1) the CTA's candidate, and its copy into every CTA's slots
         int dummy = 0;
         warp_best(bkey, blin, bval, dummy);
@@ -1095,9 +1128,33 @@ __global__ void __launch_bounds__(DT, 1) prrlu_c2d_kernel(PrrluArgs<T> a) {
             mine.lin = cl_;
             mine.pad = *sfail;
             mine.val = cv;
-            for (int t = lane; t < C; t += 32) *cl.map_shared_rank(cand + par * C + g, t) = mine;
+            if (mbx) {
+                const uint32_t slot = smem_u32addr(cand + par * C + g);
+                for (int t = lane; t < C; t += 32) st_async_cand(peer_addr(slot, t), mine, peer_addr(cb, t));
+            } else {
+                for (int t = lane; t < C; t += 32) *cl.map_shared_rank(cand + par * C + g, t) = mine;
+            }
         }
-        cl.sync();
+        if (mbx) {
+            // warp 0 waits for the C candidates; the block barrier passes its view (and the outcome,
+            // so that every thread of the CTA takes the same branch) to the other warps
+            if (warp == 0) {
+                const uint32_t cpar = (uint32_t)((p >> 1) & 1);
+                bool ok = mb_wait_bounded(cb, cpar, a.spin_limit);
+                if (!ok) {
+                    if (lane == 0) *sfail = 1;
+                    ok = mb_wait_bounded(cb, cpar, 0);
+                }
+                if (!__all_sync(0xffffffffu, ok) && lane == 0) *shard = 1;
+            }
+            __syncthreads();
+            if (*shard) {  // the exchange itself failed: this CTA stops, the others' waits run out
+                if (g == 0 && tid == 0) atomicOr(a.err, DEVERR_TIMEOUT);
+                break;
+            }
+        } else {
+            cl.sync();
+        }
         // (2) the winner among the C candidates and the step's decision, taken by every warp alike
         kbits_t wk = 0;
         int wl = INT_MAX, gw = 0, bad = 0;
@@ -1180,7 +1237,14 @@ __global__ void __launch_bounds__(DT, 1) prrlu_c2d_kernel(PrrluArgs<T> a) {
         const bool lrole = warp < ((nr + 31) >> 5);
         const bool urole = warp >= uw0 && warp < uw0 + ((nc + 31) >> 5);
         if (lrole || urole) {
-            if (!mb_wait_bounded(bar, (uint32_t)par, a.spin_limit)) *sfail = 1;  // every CTA stops at the next exchange
+            // a run-out wait is reported with the next candidate (every CTA then stops there) and
+            // waited out again with the long bound, so that no entry is still in flight to this CTA
+            bool ok = mb_wait_bounded(bar, (uint32_t)par, a.spin_limit);
+            if (!ok) {
+                *sfail = 1;
+                ok = mb_wait_bounded(bar, (uint32_t)par, 0);
+            }
+            if (!ok) *shard = 1;
         }
         const T inv = *sinv;
         // (5) multipliers of the local rows and this CTA's entries of row p of U, one thread each
@@ -1213,6 +1277,10 @@ __global__ void __launch_bounds__(DT, 1) prrlu_c2d_kernel(PrrluArgs<T> a) {
             }
         if (cj >= cw && cj < cw + CC) colmask &= ~(1u << (cj - cw));
         __syncthreads();
+        if (mbx && *shard) {  // (with the cluster barrier the steps stay in lockstep instead)
+            if (g == 0 && tid == 0) atomicOr(a.err, DEVERR_TIMEOUT);
+            break;
+        }
         // (6) Schur-complement update in registers, fused with the next local argmax: one chain per
         //     row slot; along a row the positions grow with j, so a later entry wins only with a
         //     strictly larger key, and the chain keeps the key and the column index alone. The
@@ -1255,13 +1323,6 @@ __global__ void __launch_bounds__(DT, 1) prrlu_c2d_kernel(PrrluArgs<T> a) {
             }
         }
         ++p;
-    }
-    // A wait of step p - 1 ran out (the loop then stopped at step p, before sending anything):
-    // let the entries of that step still in flight to this CTA land before it leaves (bounded).
-    if (*sfail && p > 0) {
-        const unsigned long long t0 = globaltimer_ns();
-        for (unsigned it = 0; !mb_done_cluster(bar, (uint32_t)((p - 1) & 1)); ++it)
-            if ((it & 63u) == 0 && globaltimer_ns() - t0 > kC2dWaitNs) break;
     }
     if (g == 0 && tid == 0) {
         if (a.flops) {
@@ -2003,6 +2064,18 @@ int prrlu_gridc_override() {
     return v;
 }
 
+// The 2D variant exchanges candidates through st.async stores and mbarriers (default; 2-4 % per
+// launch faster than the cluster barrier, e.g. 96 x 96: 0.225 vs 0.243 ms, 1000 x 200: 0.901 vs
+// 0.928 ms); ACI_PRRLU_MBX=0 takes the cluster barrier (launch-shape tuning only: the pivots are
+// the same).
+int prrlu_mbx_mode() {
+    static const int v = [] {
+        const char* e = std::getenv("ACI_PRRLU_MBX");
+        return e ? (std::atoi(e) != 0 ? 1 : 0) : 1;
+    }();
+    return v;
+}
+
 static int pow2_at_least(int x) {
     int p = 1;
     while (p < x) p <<= 1;
@@ -2157,6 +2230,7 @@ cudaError_t launch_prrlu(const PrrluArgs<T>& a_in, int G, cudaStream_t st) {
             a.wcap_cols = cc;
             a.wcap_elems = 0;
             a.grid_c = Cc;
+            a.c2d_mbx = prrlu_mbx_mode();
             cudaError_t e = kernel_attrs((const void*)fn);
             if (e != cudaSuccess) return e;
             cudaLaunchConfig_t cfg = {};

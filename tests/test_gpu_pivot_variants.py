@@ -5,7 +5,8 @@ Every variant of the full-search pivot kernel forms each entry with the same ope
 lowest row x n + col), so the variant chosen for a launch shape must not change a single bit of
 the pivots, D, L, U or of a whole product. The variant is fixed per process by environment
 variables read once by the library (ACI_PRRLU_2D = 0: never the 2D register kernel, 2: wherever it
-fits; ACI_PRRLU_GRIDC / ACI_PRRLU_CLUSTER: its column groups / the cluster size), so each
+fits; ACI_PRRLU_GRIDC / ACI_PRRLU_CLUSTER: its column groups / the cluster size; ACI_PRRLU_MBX:
+its candidate exchange through mbarriers or the cluster barrier), so each
 configuration runs in a child process; the default configuration is compared with the oracle in
 test_gpu_kernels.py and test_gpu_aci.py."""
 
@@ -60,7 +61,7 @@ np.savez(sys.argv[2], **out)
 
 def _run(env_extra, path):
     env = dict(os.environ)
-    for v in ("ACI_PRRLU_2D", "ACI_PRRLU_GRIDC", "ACI_PRRLU_CLUSTER"):
+    for v in ("ACI_PRRLU_2D", "ACI_PRRLU_GRIDC", "ACI_PRRLU_CLUSTER", "ACI_PRRLU_MBX"):
         env.pop(v, None)
     env.update(env_extra)
     r = subprocess.run([sys.executable, "-c", CHILD, ROOT, str(path), repr(CASES)], env=env, cwd=ROOT,
@@ -79,7 +80,9 @@ def default_run(tmp_path_factory):
 @pytest.mark.parametrize("env", [{"ACI_PRRLU_2D": "0"}, {"ACI_PRRLU_2D": "2"},
                                  {"ACI_PRRLU_2D": "2", "ACI_PRRLU_GRIDC": "2"},
                                  {"ACI_PRRLU_2D": "2", "ACI_PRRLU_GRIDC": "8"},
-                                 {"ACI_PRRLU_2D": "2", "ACI_PRRLU_CLUSTER": "4"}, {"ACI_PRRLU_CLUSTER": "8"}])
+                                 {"ACI_PRRLU_2D": "2", "ACI_PRRLU_CLUSTER": "4"}, {"ACI_PRRLU_CLUSTER": "8"},
+                                 {"ACI_PRRLU_2D": "2", "ACI_PRRLU_MBX": "1"},
+                                 {"ACI_PRRLU_2D": "2", "ACI_PRRLU_MBX": "0"}])
 def test_variants_are_bit_identical(default_run, env, tmp_path):
     other = _run(env, tmp_path / "variant.npz")
     assert sorted(default_run.files) == sorted(other.files)
