@@ -2217,14 +2217,15 @@ cudaError_t launch_prrlu(const PrrluArgs<T>& a_in, int G, cudaStream_t st) {
         const int wneed = (a.nmax + C - 1) / C;
         const int rows = (a.mmax + RT - 1) / RT;
         // The 2D variant where it measured faster than the 1D register variant (per launch, GB300):
-        // complex blocks, real blocks of more than 512 rows, and real blocks whose 1D split leaves at
-        // most 8 columns per CTA; the 1D variant keeps real blocks of up to 512 rows and 9-32 columns
-        // per CTA (at 480 x 480 it took 1.37 ms against 1.52). ACI_PRRLU_2D = 2 takes the 2D variant
-        // wherever it fits, 0 nowhere.
-        const bool prefer2d = cp || rows > 1 || wneed <= 8;
+        // complex blocks, real blocks of more than 512 rows, real blocks whose 1D split leaves at
+        // most 8 columns per CTA, and real blocks whose 2D tile holds at most 8 values per thread
+        // (256 x 256: 0.476 vs 0.508 ms); the 1D variant keeps the larger real blocks of up to 512
+        // rows (480 x 480: 1.36 vs 1.56 ms, 480 x 246: 0.83 vs 0.87). ACI_PRRLU_2D = 2 takes the 2D
+        // variant wherever it fits, 0 nowhere.
         int Cr = 0, Cc = 0, rr = 0, cc = 0;
-        if ((prrlu_2d_mode() == 2 || (prrlu_2d_mode() == 1 && prefer2d)) &&
-            c2d_plan<T>(a.mmax, a.nmax, cmax, &Cr, &Cc, &rr, &cc)) {
+        const bool fits2d = c2d_plan<T>(a.mmax, a.nmax, cmax, &Cr, &Cc, &rr, &cc);
+        const bool prefer2d = cp || rows > 1 || wneed <= 8 || rr * cc <= 8;
+        if (fits2d && (prrlu_2d_mode() == 2 || (prrlu_2d_mode() == 1 && prefer2d))) {
             void (*fn)(PrrluArgs<T>) = c2d_kernel<T>(rr, cc);
             a.epc = 0;
             a.wcap_cols = cc;
