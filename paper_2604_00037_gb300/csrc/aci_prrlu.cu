@@ -216,6 +216,15 @@ __device__ __forceinline__ void block_argmax(kbits_t& key, int& lin, kbits_t* sk
     lin = slin[NWARP];
 }
 
+// Multiply-adds of p Schur-complement updates of an m x n block, sum over q < p of
+// (m - q - 1)(n - q - 1), in closed form (exact in 64-bit integers for m, n <= 65536, p <= 8192):
+// a loop of dependent FP64 additions would sit on the kernel's tail.
+__device__ __forceinline__ double schur_mults(int m, int n, int p) {
+    const long long a = m - 1, b = n - 1, q = p;
+    const long long s1 = q * (q - 1) / 2, s2 = (q - 1) * q * (2 * q - 1) / 6;
+    return (double)(q * a * b - (a + b) * s1 + s2);
+}
+
 __host__ __device__ inline int live_ctas(long long mn, int n, int G, int epc) {
     long long g = (mn + epc - 1) / epc;
     if (g < 1) g = 1;
@@ -425,8 +434,7 @@ __global__ void __launch_bounds__(PT) prrlu_kernel(PrrluArgs<T> a) {
     if (g == 0 && tid == 0) {
         if (a.flops) {  // Schur-update multiply-adds: sum_{q<p} (m-q-1)(n-q-1)
             const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
-            double f = 0.0;
-            for (int q = 0; q < p; ++q) f += (double)(m - q - 1) * (double)(n - q - 1);
+            const double f = schur_mults(m, n, p);
             atomicAdd(a.flops, per * f);
         }
         *a.eps_out = eps;
@@ -635,8 +643,7 @@ __global__ void __launch_bounds__(PT) prrlu_cluster_kernel(PrrluArgs<T> a) {
     if (g == 0 && tid == 0) {
         if (a.flops) {
             const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
-            double f = 0.0;
-            for (int q = 0; q < p; ++q) f += (double)(m - q - 1) * (double)(n - q - 1);
+            const double f = schur_mults(m, n, p);
             atomicAdd(a.flops, per * f);
         }
         *a.eps_out = eps;
@@ -877,8 +884,7 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
     if (g == 0 && tid == 0) {
         if (a.flops) {
             const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
-            double f = 0.0;
-            for (int q = 0; q < p; ++q) f += (double)(m - q - 1) * (double)(n - q - 1);
+            const double f = schur_mults(m, n, p);
             atomicAdd(a.flops, per * f);
         }
         *a.eps_out = eps;
@@ -1327,8 +1333,7 @@ __global__ void __launch_bounds__(DT, 1) prrlu_c2d_kernel(PrrluArgs<T> a) {
     if (g == 0 && tid == 0) {
         if (a.flops) {
             const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
-            double f = 0.0;
-            for (int q = 0; q < p; ++q) f += (double)(m - q - 1) * (double)(n - q - 1);
+            const double f = schur_mults(m, n, p);
             atomicAdd(a.flops, per * f);
         }
         *a.eps_out = eps;
@@ -1513,8 +1518,7 @@ __global__ void __launch_bounds__(CT, 1) prrlu_cta_kernel(PrrluArgs<T> a) {
     if (tid == 0) {
         if (a.flops) {
             const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
-            double f = 0.0;
-            for (int q = 0; q < p; ++q) f += (double)(m - q - 1) * (double)(n - q - 1);
+            const double f = schur_mults(m, n, p);
             atomicAdd(a.flops, per * f);
         }
         *a.eps_out = eps;
