@@ -905,7 +905,8 @@ def main():
     wall = dinfo["device_ms"]
     roofline = {"bound": "alu", "kernel": {"frame": "gemm_kernel (frame half-products)",
                                            "pi": "gemm_kernel (Pi block + f)",
-                                           "pivot": "prrlu_creg_kernel / prrlu_cluster_kernel / prrlu_kernel"}[dom],
+                                           "pivot": "pivot search: prrlu_creg_kernel (1D) / prrlu_c2d_kernel (2D) / "
+                                                    "prrlu_cta_kernel (single CTA), chosen per launch"}[dom],
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                 "traffic": traffic,
                 "traffic_note": ("DRAM bytes per launch: the ncu ratio of DRAM bytes to input-block bytes "
