@@ -25,6 +25,7 @@
 // a distinct tag base.
 // The Schur update of step p is fused with the local argmax of step p+1.
 #include <algorithm>
+#include <cfloat>
 #include <climits>
 #include <cstdlib>
 #include <mutex>
@@ -152,11 +153,44 @@ __device__ __forceinline__ cplx recip_of(cplx d) {
     return mkc(d.re * r, -d.im * r);
 }
 
-// The stop test of Algorithm 2 and the multiplier scale for the step's winner. For real values
-// |pivot| <= tau and pivot == 0 are decided on the key bits (exact: keys are non-negative
-// doubles), which keeps FP64 compares (~170 cycles each here) off the critical path.
+// The stop test |pivot| <= tau as a compare on key bits. Real keys are |v|. A complex key is
+// re*re + im*im (each rounded) and |v| is its correctly rounded square root, which is monotone:
+// sqrt(key) <= tau exactly when key <= K(tau), the largest double whose root is at most tau. K(tau)
+// is found once per launch (a few square roots near tau * tau), so no step takes a square root.
+__device__ inline kbits_t tau_key(double tau, double) { return key_bits(tau); }
+__device__ inline kbits_t tau_key(double tau, cplx) {
+    if (!(tau >= 0.0)) return 0;
+    if (isinf(tau)) return key_bits(INFINITY);
+    double k = __dmul_rn(tau, tau);
+    while (k > 0.0 && __dsqrt_rn(k) > tau) k = nextafter(k, 0.0);
+    while (k < DBL_MAX && __dsqrt_rn(nextafter(k, INFINITY)) <= tau) k = nextafter(k, INFINITY);
+    return key_bits(k);
+}
+// K(tau) for every thread of the CTA: thread 0 forms it (complex) and a block barrier shares it.
+// Called by all threads of the CTA alike.
 template <class T>
-__device__ __forceinline__ void decide(Decision<T>* d, kbits_t wkey, int wlin, T piv, int p, int kmax, double tau,
+__device__ __forceinline__ kbits_t tau_key_cta(double tau) {
+    if constexpr (sizeof(T) == sizeof(double)) {
+        return key_bits(tau);
+    } else {
+        __shared__ kbits_t s_tkey;
+        if (threadIdx.x == 0) s_tkey = tau_key(tau, T());
+        __syncthreads();
+        return s_tkey;
+    }
+}
+// pivot == 0 on the bits (both parts +-0), no FP64 compare
+__device__ __forceinline__ bool val_is_zero(double v) { return (((unsigned long long)__double_as_longlong(v)) << 1) == 0; }
+__device__ __forceinline__ bool val_is_zero(cplx v) {
+    return ((((unsigned long long)__double_as_longlong(v.re)) | ((unsigned long long)__double_as_longlong(v.im))) << 1) == 0;
+}
+
+// The stop test of Algorithm 2 and the multiplier scale for the step's winner: |pivot| <= tau
+// (tkey = tau_key(tau)) and pivot == 0 are decided on bits, and |pivot| (a square root for complex
+// values) is formed only at the stop, which keeps FP64 work (~64 cycles per warp-wide operation
+// here, in every warp that takes the decision) off the steps.
+template <class T>
+__device__ __forceinline__ void decide(Decision<T>* d, kbits_t wkey, int wlin, T piv, int p, int kmax, kbits_t tkey,
                                        bool with_inv = true) {
     int code = 0;
     double e = 0.0;
@@ -165,16 +199,18 @@ __device__ __forceinline__ void decide(Decision<T>* d, kbits_t wkey, int wlin, T
     if (wlin == INT_MAX) {
         code = 1;
     } else {
-        const double mag = key_to_mag(__longlong_as_double((long long)wkey), T());
-        const bool is_real = sizeof(T) == sizeof(double);
-        const bool below = is_real ? (wkey <= key_bits(tau)) : (mag <= tau);
-        const bool zero = is_real ? (wkey == 0) : s_iszero(piv);
+        // pivot == 0 from the key bits where they decide it (real: the key is |pivot|; complex: a
+        // nonzero key rules it out), so the common step does not wait for the value's shuffle (in
+        // the real path that wait cost 3.5 % of the bench product)
+        constexpr bool is_real = sizeof(T) == sizeof(double);
+        const bool below = wkey <= tkey;
+        const bool zero = is_real ? (wkey == 0) : (wkey == 0 && val_is_zero(piv));
         if (wkey >= key_bits(INFINITY)) {
             code = 2;
-            e = mag;
+            e = key_to_mag(__longlong_as_double((long long)wkey), T());
         } else if (p == kmax || (p >= 1 && below)) {
             code = 1;
-            e = mag;
+            e = key_to_mag(__longlong_as_double((long long)wkey), T());
         } else if (zero) {
             d->zpiv = 1;
         } else if (with_inv) {
@@ -298,6 +334,7 @@ __global__ void __launch_bounds__(PT) prrlu_kernel(PrrluArgs<T> a) {
     const int kmax = min(min(m, n), a.chimax);
     const double S = a.rel ? __longlong_as_double((long long)*a.smax) : 0.0;
     const double tau = a.rel ? a.tol * S : a.tol;
+    const kbits_t tkey = threadIdx.x == 0 ? tau_key(tau, T()) : 0;  // thread 0 takes the decision
 
     int p = 0;
     double eps = 0.0;
@@ -347,7 +384,7 @@ __global__ void __launch_bounds__(PT) prrlu_kernel(PrrluArgs<T> a) {
                 piv = sval[gw];
             }
         }
-        if (tid == 0) decide(dec, wkey, wlin, piv, p, kmax, tau);
+        if (tid == 0) decide(dec, wkey, wlin, piv, p, kmax, tkey);
         __syncthreads();
         if (dec->code) {  // stop: no unused entry left, tolerance or rank cap reached, or non-finite
             if (dec->code == 2 && g == 0 && tid == 0) atomicOr(a.err, DEVERR_NUMERIC);
@@ -510,6 +547,7 @@ __global__ void __launch_bounds__(PT) prrlu_cluster_kernel(PrrluArgs<T> a) {
     const int kmax = min(min(m, n), a.chimax);
     const double S = a.rel ? __longlong_as_double((long long)*a.smax) : 0.0;
     const double tau = a.rel ? a.tol * S : a.tol;
+    const kbits_t tkey = threadIdx.x == 0 ? tau_key(tau, T()) : 0;  // thread 0 takes the decision
 
     int p = 0;
     double eps = 0.0;
@@ -563,7 +601,7 @@ __global__ void __launch_bounds__(PT) prrlu_cluster_kernel(PrrluArgs<T> a) {
                 wbest[NWARP].lin = l;
                 wbest[NWARP].pad = src;
                 wbest[NWARP].val = pv;
-                decide(dec, k, l, pv, p, kmax, tau);
+                decide(dec, k, l, pv, p, kmax, tkey);
             }
         }
         __syncthreads();
@@ -757,6 +795,7 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
     const int kmax = min(min(m, n), a.chimax);
     const double S = a.rel ? __longlong_as_double((long long)*a.smax) : 0.0;
     const double tau = a.rel ? a.tol * S : a.tol;
+    const kbits_t tkey = tau_key_cta<T>(tau);  // every warp takes the decision
 
     int p = 0;
     double eps = 0.0;
@@ -805,7 +844,7 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
         }
         warp_best(wk, wl, pv, gw);
         Decision<T> dl;
-        decide(&dl, wk, wl, pv, p, kmax, tau, false);
+        decide(&dl, wk, wl, pv, p, kmax, tkey, false);
         if (dl.code) {
             if (dl.code == 2 && g == 0 && tid == 0) atomicOr(a.err, DEVERR_NUMERIC);
             eps = dl.eps;
@@ -1105,6 +1144,7 @@ __global__ void __launch_bounds__(DT, 1) prrlu_c2d_kernel(PrrluArgs<T> a) {
     const int kmax = min(min(m, n), a.chimax);
     const double S = a.rel ? __longlong_as_double((long long)*a.smax) : 0.0;
     const double tau = a.rel ? a.tol * S : a.tol;
+    const kbits_t tkey = tau_key_cta<T>(tau);  // every warp takes the decision
     const uint32_t rbytes = (uint32_t)(((size_t)nr + (size_t)nc) * sizeof(T));
     if (mbx) cl.sync();  // every CTA's mbarriers are initialised before any CTA signals one
 
@@ -1179,7 +1219,7 @@ __global__ void __launch_bounds__(DT, 1) prrlu_c2d_kernel(PrrluArgs<T> a) {
         }
         warp_best(wk, wl, pv, gw);
         Decision<T> dl;
-        decide(&dl, wk, wl, pv, p, kmax, tau, false);
+        decide(&dl, wk, wl, pv, p, kmax, tkey, false);
         if (dl.code) {
             if (dl.code == 2 && g == 0 && tid == 0) atomicOr(a.err, DEVERR_NUMERIC);
             eps = dl.eps;
@@ -1400,6 +1440,7 @@ __global__ void __launch_bounds__(CT, 1) prrlu_cta_kernel(PrrluArgs<T> a) {
     const int kmax = min(min(m, n), a.chimax);
     const double S = a.rel ? __longlong_as_double((long long)*a.smax) : 0.0;
     const double tau = a.rel ? a.tol * S : a.tol;
+    const kbits_t tkey = tau_key_cta<T>(tau);  // every warp takes the decision
 
     int p = 0;
     double eps = 0.0;
@@ -1429,7 +1470,7 @@ __global__ void __launch_bounds__(CT, 1) prrlu_cta_kernel(PrrluArgs<T> a) {
         }
         warp_best(wk, wl, pv, gw);
         Decision<T> dl;
-        decide(&dl, wk, wl, pv, p, kmax, tau, false);
+        decide(&dl, wk, wl, pv, p, kmax, tkey, false);
         if (dl.code) {
             if (dl.code == 2 && tid == 0) atomicOr(a.err, DEVERR_NUMERIC);
             eps = dl.eps;
@@ -1732,6 +1773,7 @@ __global__ void __launch_bounds__(RKT, 1) prrlu_rook_kernel(PrrluArgs<T> a) {
     const int kmin = m < n ? m : n;
     const double S = a.rel ? __longlong_as_double((long long)*a.smax) : 0.0;
     const double tau = a.rel ? a.tol * S : a.tol;
+    const kbits_t tkey = threadIdx.x == 0 ? tau_key(tau, T()) : 0;  // thread 0 takes the decision
     // scratch: two residual columns, two residual rows, used flags (see prrlu_rook_scratch_bytes)
     T* colbuf[2] = {a.W, a.W + a.mmax};
     T* rowbuf[2] = {a.W + 2 * (size_t)a.mmax, a.W + 2 * (size_t)a.mmax + a.nmax};
@@ -1823,7 +1865,7 @@ __global__ void __launch_bounds__(RKT, 1) prrlu_rook_kernel(PrrluArgs<T> a) {
         }
         // the pivot and the stop test (Algorithm 2, reading R2 with the rook pivot)
         if (threadIdx.x == 0) {
-            decide(dec, key_of(pv), r, pv, p, a.chimax, tau);
+            decide(dec, key_of(pv), r, pv, p, a.chimax, tkey);
             dec->piv = pv;
         }
         __syncthreads();
