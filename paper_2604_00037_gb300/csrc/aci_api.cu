@@ -1369,10 +1369,13 @@ struct Run {
         aa.d = dd;
         aa.bonds = bonds_dev;
         aa.Y = Yptr_dev;
-        int Rmax = 1;
-        for (int s = 0; s < L; ++s) Rmax = std::max(Rmax, cap[s] * d[s]);
+        int Rmax = 1, Kmax = 1;
+        for (int s = 0; s < L; ++s) {
+            Rmax = std::max(Rmax, cap[s] * d[s]);
+            Kmax = std::max(Kmax, cap[s + 1]);
+        }
         cudaEvent_t e = pre(ACI_KCLASS_OTHER);
-        aci::launch_assemble<T>(aa, Rmax, st);
+        aci::launch_assemble<T>(aa, Rmax, Kmax, st);
         post(ACI_KCLASS_OTHER, e, "assemble");
         return finish(out, stats, out_memory, it, converged, fixed, launches0, &fl);
     }

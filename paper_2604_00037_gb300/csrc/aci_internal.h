@@ -211,7 +211,8 @@ template <class T> struct AssembleArgs {
     const BondBuf<T>* bonds;  // [L-1] device array
     T* const* Y;      // [L] device array of output pointers
 };
-template <class T> void launch_assemble(const AssembleArgs<T>& a, int Rmax, cudaStream_t st);
+// Rmax: the largest rows chi_s d_s of a site, Kmax: the largest rank chi_{s+1} (capacities).
+template <class T> void launch_assemble(const AssembleArgs<T>& a, int Rmax, int Kmax, cudaStream_t st);
 
 // Y = T P^-1 with dense LI, D, UJ (k x k row-major): step-level entry point.
 template <class T> void launch_apply_pinv(const T* Tm, int R, int k, const T* LI, const T* D,

@@ -74,6 +74,149 @@ __global__ void assemble_kernel(AssembleArgs<T> a) {
     solve_row<T>(xval, kout, li, uj, dv, y);
 }
 
+// The same solves with one warp per output row: lane l holds the row's
+// columns l, l + 32, ... in registers, and both solves run column by column, so that the updates of
+// a step are independent multiply-adds across lanes instead of one thread's chain of k^2 dependent
+// ones. Forward: once w_p is final it goes to every lane by a shuffle and each lane subtracts
+// w_p UJ[p, q] from its columns q > p (per column the terms come in ascending p, as in
+// solve_row). Backward: y_q, final once every q' > q is applied, goes out the same way and each
+// lane subtracts y_q LI[q, p] from its p < q (terms in descending q). Column groups of 32 that are
+// already final skip the step as a whole (a warp-wide FP64 instruction holds the pipe whatever its
+// active lanes). The CTA's 8 warps (8 rows of one site) share AT rows of UJ (columns of LI) at a
+// time, gathered into shared memory.
+constexpr int AT = 16;       // rows of UJ / columns of LI per shared-memory tile
+constexpr int AWARPS = 8;
+constexpr int AROWS = 1;     // output rows per warp
+
+template <class T, int JM>
+__device__ __forceinline__ T pick(const T (&v)[JM], int j) {
+    T r = v[0];
+#pragma unroll
+    for (int i = 1; i < JM; ++i)
+        if (i == j) r = v[i];
+    return r;
+}
+__device__ __forceinline__ double shfl_val(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ cplx shfl_val(cplx v, int src) {
+    return mkc(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
+}
+
+template <class T, int JM>
+__global__ void __launch_bounds__(AWARPS * 32) assemble_warp_kernel(AssembleArgs<T> a, int kpad) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* tile = reinterpret_cast<T*>(smem_raw);  // [AT][kpad]
+    const int s = blockIdx.y;
+    const int L = a.L;
+    const int* chi = a.chi;
+    const int ds = a.d[s];
+    const int R = chi[s] * ds;
+    const int k = chi[s + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rbase = blockIdx.x * (AWARPS * AROWS);
+    if (rbase >= R) return;  // the whole CTA alike
+    // rows of this warp (rl < 0: none)
+    int rows[AROWS];
+#pragma unroll
+    for (int w = 0; w < AROWS; ++w) {
+        const int r = rbase + warp * AROWS + w;
+        rows[w] = r < R ? r : -1;
+    }
+    // T_s rows: s = 0 -> Pi_0[sigma, J_1]; s >= 1 -> Pi_{s-1}[I_{s-1}[alpha], (sigma, :)]
+    T acc[AROWS][JM];
+#pragma unroll
+    for (int w = 0; w < AROWS; ++w) {
+        const int r = rows[w];
+#pragma unroll
+        for (int j = 0; j < JM; ++j) {
+            const int q = lane + 32 * j;
+            T x = s_zero(T());
+            if (r >= 0 && q < k) {
+                if (s == 0) {
+                    const BondBuf<T>& b0 = a.bonds[0];
+                    x = b0.Pi[(size_t)r * (a.d[1] * chi[2]) + b0.pcol[q]];
+                } else {
+                    const BondBuf<T>& bp = a.bonds[s - 1];
+                    const int alpha = r / ds, sigma = r - alpha * ds;
+                    x = bp.Pi[(size_t)bp.prow[alpha] * (ds * k) + sigma * k + q];
+                }
+            }
+            acc[w][j] = x;
+        }
+    }
+    if (s < L - 1) {
+        const BondBuf<T>& bs = a.bonds[s];
+        // forward: w UJ = x
+        for (int p0 = 0; p0 < k; p0 += AT) {
+            const int np = min(AT, k - p0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < np * k; e += AWARPS * 32) {
+                const int pp = e / k, q = e - pp * k;
+                tile[pp * kpad + q] = bs.Um[(size_t)(p0 + pp) * bs.Uld + bs.pcol[q]];
+            }
+            __syncthreads();
+            for (int pp = 0; pp < np; ++pp) {
+                const int p = p0 + pp;
+                const int jp = p >> 5, lp = p & 31;
+#pragma unroll
+                for (int w = 0; w < AROWS; ++w) {
+                    const T wp = shfl_val(pick<T, JM>(acc[w], jp), lp);
+#pragma unroll
+                    for (int j = 0; j < JM; ++j) {
+                        if (32 * j + 31 <= p || 32 * j >= k) continue;  // warp-uniform: group done or empty
+                        const int q = lane + 32 * j;
+                        if (q > p && q < k) acc[w][j] = s_fms(wp, tile[pp * kpad + q], acc[w][j]);
+                    }
+                }
+            }
+        }
+        // z = w D^-1
+#pragma unroll
+        for (int j = 0; j < JM; ++j) {
+            const int q = lane + 32 * j;
+            if (q < k) {
+                const T dq = bs.D[q];
+#pragma unroll
+                for (int w = 0; w < AROWS; ++w) acc[w][j] = s_iszero(dq) ? s_zero(T()) : s_div(acc[w][j], dq);
+            }
+        }
+        // backward: y LI = z, columns q = k-1 .. 0
+        for (int qhi = k; qhi > 0; qhi -= AT) {
+            const int q0 = max(0, qhi - AT), nq = qhi - q0;
+            __syncthreads();
+            for (int e = threadIdx.x; e < nq * k; e += AWARPS * 32) {
+                const int qq = e / k, p = e - qq * k;
+                tile[qq * kpad + p] = bs.Lm[(size_t)p * bs.Lld + bs.prow[q0 + qq]];
+            }
+            __syncthreads();
+            for (int qq = nq - 1; qq >= 0; --qq) {
+                const int q = q0 + qq;
+                const int jq = q >> 5, lq = q & 31;
+#pragma unroll
+                for (int w = 0; w < AROWS; ++w) {
+                    const T yq = shfl_val(pick<T, JM>(acc[w], jq), lq);
+#pragma unroll
+                    for (int j = 0; j < JM; ++j) {
+                        if (32 * j >= q) continue;  // warp-uniform: group done
+                        const int p = lane + 32 * j;
+                        if (p < q) acc[w][j] = s_fms(yq, tile[qq * kpad + p], acc[w][j]);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < AROWS; ++w) {
+        const int r = rows[w];
+        if (r < 0) continue;
+        T* y = a.Y[s] + (size_t)r * k;
+#pragma unroll
+        for (int j = 0; j < JM; ++j) {
+            const int q = lane + 32 * j;
+            if (q < k) y[q] = acc[w][j];
+        }
+    }
+}
+
 template <class T>
 __global__ void apply_pinv_kernel(const T* Tm, int R, int k, const T* LI, const T* D, const T* UJ, T* Y) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -251,7 +394,24 @@ void launch_gather(const GatherArgs<T>& a, long long max_elems, int num_sms, cud
 }
 
 template <class T>
-void launch_assemble(const AssembleArgs<T>& a, int Rmax, cudaStream_t st) {
+void launch_assemble(const AssembleArgs<T>& a, int Rmax, int Kmax, cudaStream_t st) {
+    // the warp-per-row kernel up to rank 256 (8 columns per lane), one thread per row above
+    const int jm = (Kmax + 31) / 32;
+    void (*fn)(AssembleArgs<T>, int) = nullptr;
+    if (jm <= 1) fn = assemble_warp_kernel<T, 1>;
+    else if (jm <= 2) fn = assemble_warp_kernel<T, 2>;
+    else if (jm <= 4) fn = assemble_warp_kernel<T, 4>;
+    else if (jm <= 8) fn = assemble_warp_kernel<T, 8>;
+    if (fn) {
+        const int kpad = std::max(1, Kmax);
+        const size_t smem = sizeof(T) * (size_t)AT * kpad;  // <= 64 KB (complex, rank 256)
+        // once per product; a failure here surfaces as the launch's error
+        if (cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return;
+        dim3 grid((Rmax + AWARPS * AROWS - 1) / (AWARPS * AROWS), a.L);
+        fn<<<grid, AWARPS * 32, smem, st>>>(a, kpad);
+        return;
+    }
     const int nt = 64;
     dim3 grid((Rmax + nt - 1) / nt, a.L);
     assemble_kernel<T><<<grid, nt, 0, st>>>(a);
@@ -286,8 +446,8 @@ void launch_iter_check(int L, const int* chi, int* chi_prev, int* const* pcol, i
 
 template void launch_gather<double>(const GatherArgs<double>&, long long, int, cudaStream_t);
 template void launch_gather<cplx>(const GatherArgs<cplx>&, long long, int, cudaStream_t);
-template void launch_assemble<double>(const AssembleArgs<double>&, int, cudaStream_t);
-template void launch_assemble<cplx>(const AssembleArgs<cplx>&, int, cudaStream_t);
+template void launch_assemble<double>(const AssembleArgs<double>&, int, int, cudaStream_t);
+template void launch_assemble<cplx>(const AssembleArgs<cplx>&, int, int, cudaStream_t);
 template void launch_apply_pinv<double>(const double*, int, int, const double*, const double*,
                                         const double*, double*, cudaStream_t);
 template void launch_apply_pinv<cplx>(const cplx*, int, int, const cplx*, const cplx*, const cplx*,
