@@ -115,7 +115,9 @@ def _compare_prrlu(g, f, M):
     # block up to 2^16 entries take the 2D register kernel, 257 x 300 and 512 x 512 real the 1D one,
     # 600 x 400 real prrlu_cluster_kernel (cluster path, too wide for either register kernel);
     # 700 x 700 real and every larger complex block take the cooperative grid prrlu_kernel
-    ((128, 300), 128, 1e-8), ((600, 400), 300, 1e-10), ((700, 700), 350, 1e-10)])
+    ((128, 300), 128, 1e-8), ((600, 400), 300, 1e-10), ((700, 700), 350, 1e-10),
+    # 160 x 400 real: the 1D register kernel with 5 of its 16 warps holding rows
+    ((160, 400), 150, 1e-10)])
 def test_prrlu_matches_oracle(ctx, cplx, shape, chimax, taurel):
     m, n = shape
     rng = np.random.default_rng(m * 1000 + n)

@@ -22,9 +22,11 @@ torch = pytest.importorskip("torch")
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-# (m, n, chimax, complex): 2D grids 4 x 4 (tiles 4 x 8, 2 x 4, 1 x 8), 8 x 2, 2 x 8, 2 x 2
+# (m, n, chimax, complex): 2D grids 4 x 4 (tiles 4 x 8, 2 x 4, 1 x 8), 8 x 2, 2 x 8, 2 x 2; the
+# 1D kernel at 480 x 480, 480 x 246 and 160 x 400
 CASES = [(480, 480, 240, False), (256, 256, 128, False), (200, 200, 100, True), (128, 300, 128, True),
-         (700, 100, 90, False), (100, 700, 90, False), (37, 53, 30, False), (480, 246, 200, False)]
+         (700, 100, 90, False), (100, 700, 90, False), (37, 53, 30, False), (480, 246, 200, False),
+         (160, 400, 150, False)]
 
 CHILD = r"""
 import sys
