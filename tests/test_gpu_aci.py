@@ -88,6 +88,16 @@ def test_fused_d8_ragged(ctx):
     compare_with_oracle(ctx, [a, b], "mul", 1e-12, 200)
 
 
+def test_assembly_above_rank_256_capacity(ctx):
+    """The output assembly takes one warp per row up to rank capacity 256 (8 columns per lane) and
+    one thread per row above it: 18 sites of d = 2 with max_rank 300 give capacity 300 at the
+    middle bonds, so the second form runs; against the oracle on 20000 points."""
+    rng = np.random.default_rng(31)
+    a = tt_random_uniform(rng, 18, 2, 4, low=-1, high=1)
+    b = tt_random_uniform(rng, 18, 2, 3, low=-1, high=1)
+    compare_with_oracle(ctx, [a, b], "mul", 1e-12, 300, dense=False)
+
+
 def test_edge_cases(ctx):
     # L = 1: y = f(x) exactly
     a = [np.array([[[1.5], [-2.0], [0.25]]])]
