@@ -253,6 +253,8 @@ template <class T> struct GatherArgs {
     unsigned long long* smax;
 };
 template <class T> void launch_gather(const GatherArgs<T>& a, long long max_elems, int num_sms, cudaStream_t st);
+// 1: pivot searches and gathers are launched with programmatic dependent launch (ACI_PDL=0: off).
+int prrlu_pdl_mode();
 
 // Pivot history of a call (aci_stats.hist_*): copies chi[kidx] pivots of one local update.
 struct HistArgs {

@@ -297,6 +297,11 @@ __global__ void iter_check_kernel(int L, const int* chi, int* chi_prev, int* con
 // ---------------------------------------------------------------- gathers of the overlapped sweep
 template <class T>
 __global__ void __launch_bounds__(256) gather_kernel(GatherArgs<T> a) {
+    // launched early behind the previous pivot search (programmatic dependent launch): wait for it
+    // before reading its pivots; then let the next pivot search start launching (it waits for this
+    // grid's completion before it reads anything)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const GatherJob<T>& j = a.job[blockIdx.y];
     const int rows = dimv(j.rows, a.chi), cols = dimv(j.cols, a.chi);
     const int sld = dimv(j.sld, a.chi), dld = dimv(j.dld, a.chi);
@@ -390,7 +395,16 @@ template <class T>
 void launch_gather(const GatherArgs<T>& a, long long max_elems, int num_sms, cudaStream_t st) {
     const long long want = (max_elems + 1023) / 1024;
     const int bx = (int)std::max(1LL, std::min(want, (long long)num_sms * 4));
-    gather_kernel<T><<<dim3(bx, a.njobs), 256, 0, st>>>(a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(bx, a.njobs);
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = prrlu_pdl_mode();
+    cudaLaunchKernelEx(&cfg, gather_kernel<T>, a);  // errors surface at the sweep's next check
 }
 
 template <class T>

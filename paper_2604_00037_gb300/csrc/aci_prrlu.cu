@@ -98,6 +98,15 @@ __device__ __forceinline__ bool get_words(const unsigned long long* p, unsigned 
     }
 }
 
+// Programmatic dependent launch: a kernel launched with the programmatic-serialization attribute
+// may start while the previous kernel of its stream finishes; it waits here, before reading any
+// of that kernel's outputs (a no-op when launched without the attribute).
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// ... and lets the next kernel of the stream, if launched so, start its launch (it waits for this
+// grid's completion before reading anything): issued after the pivot loop, so that a waiting
+// dependent never holds SMs while the search runs.
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Keys are non-negative doubles (|v|, or re^2 + im^2), so they order like their bit patterns:
 // the argmax compares 64-bit integers (the FP64 pipe, 2 ops/clk/SM on GB300, is left to the
 // Schur update). A NaN key sorts above +inf and surfaces as a numeric error at the stop test.
@@ -277,6 +286,7 @@ __device__ __forceinline__ bool small_block(const PrrluArgs<T>& a, int m, int n)
 
 template <class T, bool SMEMW>
 __global__ void __launch_bounds__(PT) prrlu_kernel(PrrluArgs<T> a) {
+    grid_dependency_wait();  // launched early behind the previous kernel of the stream: its outputs are read below
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int WPV = Words<T>::value;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x;
@@ -496,6 +506,7 @@ template <class T> struct __align__(16) Cand {
 
 template <class T, bool SMEMW>
 __global__ void __launch_bounds__(PT) prrlu_cluster_kernel(PrrluArgs<T> a) {
+    grid_dependency_wait();  // launched early behind the previous kernel of the stream: its outputs are read below
     namespace cg = cooperative_groups;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cl = cg::this_cluster();
@@ -678,6 +689,7 @@ __global__ void __launch_bounds__(PT) prrlu_cluster_kernel(PrrluArgs<T> a) {
         }
         ++p;
     }
+    grid_dependents_launch();  // the next kernel of the stream (a gather) may start launching
     if (g == 0 && tid == 0) {
         if (a.flops) {
             const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
@@ -749,6 +761,7 @@ __device__ __forceinline__ T select_reg(const T (&v)[W], int j) {
 
 template <class T, int ROWS, int WMAX>
 __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
+    grid_dependency_wait();  // launched early behind the previous kernel of the stream: its outputs are read below
     namespace cg = cooperative_groups;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cl = cg::this_cluster();
@@ -920,6 +933,7 @@ __global__ void __launch_bounds__(RT, 1) prrlu_creg_kernel(PrrluArgs<T> a) {
             if (better(qk[q], ql[q], bkey, blin)) { bkey = qk[q]; blin = ql[q]; bval = qv[q]; }
         ++p;
     }
+    grid_dependents_launch();  // the next kernel of the stream (a gather) may start launching
     if (g == 0 && tid == 0) {
         if (a.flops) {
             const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
@@ -1066,6 +1080,7 @@ size_t c2d_bytes(int rr, int cc, int C) {
 
 template <class T, int RR, int CC>
 __global__ void __launch_bounds__(DT, 1) prrlu_c2d_kernel(PrrluArgs<T> a) {
+    grid_dependency_wait();  // launched early behind the previous kernel of the stream: its outputs are read below
     namespace cg = cooperative_groups;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cl = cg::this_cluster();
@@ -1370,6 +1385,7 @@ __global__ void __launch_bounds__(DT, 1) prrlu_c2d_kernel(PrrluArgs<T> a) {
         }
         ++p;
     }
+    grid_dependents_launch();  // the next kernel of the stream (a gather) may start launching
     if (g == 0 && tid == 0) {
         if (a.flops) {
             const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
@@ -1399,6 +1415,7 @@ constexpr int CWARP = CT / 32;
 
 template <class T, int ROWS, int W>
 __global__ void __launch_bounds__(CT, 1) prrlu_cta_kernel(PrrluArgs<T> a) {
+    grid_dependency_wait();  // launched early behind the previous kernel of the stream: its outputs are read below
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m = dimv(a.m, a.chi), n = dimv(a.n, a.chi);
@@ -1556,6 +1573,7 @@ __global__ void __launch_bounds__(CT, 1) prrlu_cta_kernel(PrrluArgs<T> a) {
             if (better(qk[q], ql[q], bkey, blin)) { bkey = qk[q]; blin = ql[q]; bval = qv[q]; }
         ++p;
     }
+    grid_dependents_launch();  // the next kernel of the stream (a gather) may start launching
     if (tid == 0) {
         if (a.flops) {
             const double per = (sizeof(T) == sizeof(cplx)) ? 8.0 : 2.0;
@@ -1760,6 +1778,7 @@ __device__ RkCand<T> rk_eval(const PrrluArgs<T>& a, const unsigned char* used, i
 
 template <class T>
 __global__ void __launch_bounds__(RKT, 1) prrlu_rook_kernel(PrrluArgs<T> a) {
+    grid_dependency_wait();  // launched early behind the previous kernel of the stream: its outputs are read below
     extern __shared__ __align__(16) unsigned char rk_smem[];
     const int kcap_s = a.wcap_cols;  // shared capacity of the pivot and weight vectors
     T* Ds = reinterpret_cast<T*>(rk_smem);
@@ -2122,6 +2141,17 @@ int prrlu_mbx_mode() {
     return v;
 }
 
+// Pivot-search launches of the cluster and single-CTA variants carry the programmatic-serialization
+// attribute (the kernel's launch overlaps the end of the previous kernel of the stream, the gather;
+// it waits in grid_dependency_wait before reading); ACI_PDL=0 turns that off.
+int prrlu_pdl_mode() {
+    static const int v = [] {
+        const char* e = std::getenv("ACI_PDL");
+        return e ? (std::atoi(e) != 0 ? 1 : 0) : 1;
+    }();
+    return v;
+}
+
 static int pow2_at_least(int x) {
     int p = 1;
     while (p < x) p <<= 1;
@@ -2214,6 +2244,11 @@ cudaError_t launch_small(PrrluArgs<T>& a, cudaStream_t st, bool* covers) {
     cfg.blockDim = dim3(CT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = prrlu_pdl_mode();
     return cudaLaunchKernelEx(&cfg, fn, a);
 }
 
@@ -2285,25 +2320,29 @@ cudaError_t launch_prrlu(const PrrluArgs<T>& a_in, int G, cudaStream_t st) {
             cfg.blockDim = dim3(DT);
             cfg.dynamicSmemBytes = c2d_bytes<T>(rr, cc, Cr * Cc);
             cfg.stream = st;
-            cudaLaunchAttribute at[1];
+            cudaLaunchAttribute at[2];
             at[0].id = cudaLaunchAttributeClusterDimension;
             at[0].val.clusterDim.x = Cr * Cc;
             at[0].val.clusterDim.y = 1;
             at[0].val.clusterDim.z = 1;
+            at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[1].val.programmaticStreamSerializationAllowed = 1;
             cfg.attrs = at;
-            cfg.numAttrs = 1;
+            cfg.numAttrs = 1 + prrlu_pdl_mode();
             return cudaLaunchKernelEx(&cfg, fn, a);
         }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(C);
         cfg.stream = st;
-        cudaLaunchAttribute at[1];
+        cudaLaunchAttribute at[2];
         at[0].id = cudaLaunchAttributeClusterDimension;
         at[0].val.clusterDim.x = C;
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[1].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = 1 + prrlu_pdl_mode();
         void (*reg)(PrrluArgs<T>) = nullptr;
         int wmax = 0;
         // register budget: at most 32 values per thread (real) or 16 (complex)
