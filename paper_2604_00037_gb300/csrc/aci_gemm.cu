@@ -79,6 +79,10 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];
     __shared__ int s_last;
+    // programmatic dependent launch: wait for the previous kernel of the stream before reading
+    // anything (the plan reads the device-resolved ranks), then let the next one start launching
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const Plan pl = make_plan(g);
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
@@ -243,7 +247,16 @@ template <class T>
 void launch_gemm(const GemmArgs<T>& g, int Mmax, int Nmax, cudaStream_t st) {
     if (Mmax <= 0 || Nmax <= 0) return;
     const int grid = 2 * g.num_sms;
-    gemm_kernel<T><<<grid, NT, 0, st>>>(g);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NT);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = prrlu_pdl_mode();
+    cudaLaunchKernelEx(&cfg, gemm_kernel<T>, g);  // errors surface at the sweep's next check
 }
 
 template void launch_gemm<double>(const GemmArgs<double>&, int, int, cudaStream_t);
