@@ -87,6 +87,16 @@ struct Fail {
     aci_status st;
 };
 
+// SMs the side stream's contractions leave to the pivot search running beside them (its largest
+// cluster); ACI_SIDE_RESERVE overrides it (launch-shape tuning only: results do not change).
+int side_reserve() {
+    static const int v = [] {
+        const char* e = std::getenv("ACI_SIDE_RESERVE");
+        return e ? std::max(0, std::atoi(e)) : 16;
+    }();
+    return v;
+}
+
 void fail(aci_ctx* ctx, aci_status st, const std::string& msg) {
     ctx->err = msg;
     throw Fail{st};
@@ -627,7 +637,11 @@ struct Run {
         g.part = gpart;
         g.tile_count = gcount;
         g.target_units = aci::gemm_target_units(ctx->num_sms, units_per_sm(Mmax, Nmax, Kmax, g.nprod, g.combine));
-        g.num_sms = ctx->num_sms;
+        // On the side stream a pivot search holds up to 16 SMs (its CTAs take nearly the whole
+        // register file): a persistent grid over all SMs would leave ~32 of its CTAs waiting for
+        // the search to end, each holding a fixed share of the units, so the contraction would
+        // take two rounds. Its grid covers only the SMs the search leaves free.
+        g.num_sms = (ctx->side && st == ctx->side) ? std::max(1, ctx->num_sms - side_reserve()) : ctx->num_sms;
         cudaEvent_t e = pre(cls);
         if (digits) {
             ck(ctx, aci::launch_gemm_tc<T>(g, Mmax, Nmax, Kmax, digits, tcbuf, tc_bytes, err,
