@@ -530,16 +530,10 @@ struct Run {
         auto it = ctx->tc_widths.find(shape_key(M, N, K, nprod, combine) ^ ((unsigned long long)digits << 40));
         return it == ctx->tc_widths.end() ? 0 : it->second;
     }
-    // the tuned choice of a shape class: units per SM in the low byte, the K-chunk cap above it
     int units_per_sm(int M, int N, int K, int nprod, int combine) const {
         if (ctx->gemm_units.empty()) return aci::kGemmUnitsPerSm;
         auto it = ctx->gemm_units.find(shape_key(M, N, K, nprod, combine));
-        return it == ctx->gemm_units.end() ? aci::kGemmUnitsPerSm : (it->second & 0xFF);
-    }
-    int kc_cap_of(int M, int N, int K, int nprod, int combine) const {
-        if (ctx->gemm_units.empty()) return 0;
-        auto it = ctx->gemm_units.find(shape_key(M, N, K, nprod, combine));
-        return it == ctx->gemm_units.end() ? 0 : (it->second >> 8);
+        return it == ctx->gemm_units.end() ? aci::kGemmUnitsPerSm : it->second;
     }
     // Time every candidate granularity on each untuned shape class of this call (operands of the
     // class's size, zero-filled: the FP64 pipe's timing does not depend on the values) and keep the
@@ -591,20 +585,14 @@ struct Run {
                 g.num_sms = ctx->num_sms;
                 int best = digits ? 0 : aci::kGemmUnitsPerSm;
                 float best_ms = 1e30f;
-                // FP64: units per SM x K-chunk cap (0: none); caps at or above the K chunks the
-                // shape has (K / 8) change nothing and are skipped
-                static const int caps[] = {0, 4, 1};
-                const int maxkc = (sh.K + 7) / 8;
-                const int ncand = digits ? 2 : 4 * 3;
+                const int ncand = digits ? 2 : 4;
                 for (int ci = 0; ci < ncand; ++ci) {
-                    const int c = digits ? widths[ci] : (cand[ci % 4] | (caps[ci / 4] << 8));
+                    const int c = digits ? widths[ci] : cand[ci];
                     if (digits) {
                         const aci::TcPlan q = aci::tc_plan(digits, is_cplx, sh.M, sh.N, sh.K, sh.nprod, sh.combine, c);
                         if (!q.ok || q.NT != c || aci::tc_scratch_bytes(q) > tc_bytes) continue;
                     } else {
-                        if (caps[ci / 4] > 0 && caps[ci / 4] >= maxkc) continue;
-                        g.target_units = aci::gemm_target_units(ctx->num_sms, c & 0xFF);
-                        g.kc_cap = c >> 8;
+                        g.target_units = aci::gemm_target_units(ctx->num_sms, c);
                     }
                     auto launch = [&]() {
                         if (digits)
@@ -649,7 +637,6 @@ struct Run {
         g.part = gpart;
         g.tile_count = gcount;
         g.target_units = aci::gemm_target_units(ctx->num_sms, units_per_sm(Mmax, Nmax, Kmax, g.nprod, g.combine));
-        g.kc_cap = kc_cap_of(Mmax, Nmax, Kmax, g.nprod, g.combine);
         // On the side stream a pivot search holds up to 16 SMs (its CTAs take nearly the whole
         // register file): a persistent grid over all SMs would leave ~32 of its CTAs waiting for
         // the search to end, each holding a fixed share of the units, so the contraction would

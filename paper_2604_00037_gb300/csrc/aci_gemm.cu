@@ -69,7 +69,6 @@ __device__ __forceinline__ Plan make_plan(const GemmArgs<T>& g) {
     const int per_kc = g.combine ? tiles_total * nq : tiles_total;
     int kc = (g.target_units + per_kc - 1) / (per_kc > 0 ? per_kc : 1);
     kc = kc < 1 ? 1 : (kc > maxkc ? maxkc : kc);
-    if (g.kc_cap > 0 && kc > g.kc_cap) kc = g.kc_cap;
     pl.kc = kc;
     pl.units = per_kc * kc;
     return pl;

@@ -25,13 +25,11 @@ template <class T> struct GemmArgs {
     int* tile_count;           // zeroed counters: gemm_tile_counters(...) of them (left zeroed)
     int target_units;          // gemm_target_units(num_sms)
     int num_sms;
-    int kc_cap;                // > 0: at most this many K chunks per product (0: as target_units gives)
 };
 
 template <class T> void launch_gemm(const GemmArgs<T>& g, int Mmax, int Nmax, cudaStream_t st);
 // Split-K granularity: about per_sm work units per SM (default kGemmUnitsPerSm; the contraction
-// tuner of aci_opts.autotune chooses among 1, 2, 4 and 8 per shape class, and a cap of the K
-// chunks, none, 4 or 1, for shapes small enough that every granularity splits K to the end).
+// tuner of aci_opts.autotune chooses among 1, 2, 4 and 8 per shape class).
 constexpr int kGemmUnitsPerSm = 4;
 constexpr int kGemmMaxUnitsPerSm = 8;
 int gemm_target_units(int num_sms, int per_sm = kGemmUnitsPerSm);
