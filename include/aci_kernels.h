@@ -110,8 +110,9 @@ aci_status aci_k_apply_pinv(aci_ctx *ctx, int32_t dtype, const void *T, int32_t 
                             const void *LI, const void *D, const void *UJ, void *Y);
 
 /* The reciprocal 1/x the pivot search uses for its multipliers (Algorithm 2's Schur step
- * divides by the pivot): an FP32 seed refined by two Newton-Raphson steps in FP64, within two
- * units in the last place of 1/x for |x| in (1e-30, 1e30) and the correctly rounded 1/x outside.
+ * divides by the pivot): the hardware's approximate FP64 reciprocal refined by two Newton-Raphson
+ * steps in FP64, within two units in the last place of 1/x for |x| in (1e-30, 1e30) and the
+ * correctly rounded 1/x outside.
  * x and y are device arrays of n doubles. */
 aci_status aci_k_reciprocal(aci_ctx *ctx, const double *x, int32_t n, double *y);
 
@@ -120,9 +121,12 @@ aci_status aci_k_reciprocal(aci_ctx *ctx, const double *x, int32_t n, double *y)
  * tensor-core pipeline is bounded; when the bound is reached the kernel records a timeout, leaves
  * its copies in flight to finish (their own wait keeps the default bound), returns, and the call
  * returns ACI_E_TIMEOUT with its outputs untouched. exchange_polls > 0 bounds the pivot search's
- * inter-CTA exchange waits (cooperative grid variant) to that many polls; pipeline_polls > 0 bounds
- * the tensor-core contraction's copy and multiply waits likewise; 0 restores the default (2^24 polls,
- * 2 s). Small values make an ordinary call run its waits out. Negative values give ACI_E_ARG. */
+ * inter-CTA exchange waits to that many polls (the cooperative grid variant's tagged words; the 2D
+ * register variant's candidate and pushed row / column mbarriers, as non-blocking tests);
+ * pipeline_polls > 0 bounds the tensor-core contraction's copy and multiply waits likewise; 0
+ * restores the defaults (2^24 polls; 1 s for the 2D variant's waits, 2 s for the tensor-core
+ * pipeline's). Small values make an ordinary call run its waits out. Negative values give
+ * ACI_E_ARG. */
 aci_status aci_set_wait_limits(aci_ctx *ctx, int64_t exchange_polls, int64_t pipeline_polls);
 
 /* Throughput of the FP64 pipe (no counterpart in the paper: the denominator of the FP64
