@@ -160,7 +160,7 @@ def test_apply_pinv(ctx, cplx):
 
 
 def test_pivot_reciprocal_within_two_ulp(ctx):
-    """The pivot search's reciprocal (FP32 seed + two Newton-Raphson steps) against 1/x."""
+    """The pivot search's reciprocal (approximate FP64 seed + two Newton-Raphson steps) against 1/x."""
     rng = np.random.default_rng(17)
     x = np.concatenate([rng.uniform(-1, 1, 4000) * 10.0 ** rng.uniform(-29, 29, 4000),
                         [1.0, -3.0, 0.1, 1e-200, -1e250, 1e-300]])
